@@ -1,0 +1,804 @@
+// C ABI of libgrover_mps.so (declared in include/grover_mps.h): argument
+// validation, the per-handle device arena, launch configuration and status
+// propagation.  All compute runs in gmps_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/grover_mps.h"
+#include "gmps_internal.h"
+
+using namespace gmps;
+
+namespace gmps {
+long long launches_so_far();
+}
+
+static thread_local std::string g_err;
+
+static gmps_status fail(gmps_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+static gmps_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(GMPS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CUDA_TRY(x)                                   \
+  do {                                                \
+    cudaError_t e_ = (x);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x);  \
+  } while (0)
+
+static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+// eps of the rank rule sigma_i > max(tol, max(m,n) eps) sigma_0: the unit of
+// the storage precision (FP32 for complex64, 2^-46 for double-word, FP64).
+static double trunc_eps_for(int dtype) {
+  if (dtype == GMPS_C64_F64SVD) return 1.1920928955078125e-07;
+  if (dtype == GMPS_DW) return 1.4210854715202004e-14;
+  return 2.220446049250313e-16;
+}
+
+// ---------------------------------------------------------------- sizing
+struct Plan {
+  int chicap, xcap, threads, resident;
+  size_t smem, site_elems, elem_bytes;
+  std::vector<long long> off;  // n+1
+};
+
+static int xcap_for(int apply, int M, int chicap) {
+  if (apply == GMPS_APPLY_MPO) return (M + 1) * chicap;
+  if (apply == GMPS_APPLY_SPLIT) return chicap + M;
+  return chicap + M + 1;
+}
+
+static int auto_threads(int xcap) {
+  if (xcap <= 8) return 32;
+  if (xcap <= 16) return 64;
+  if (xcap <= 32) return 128;
+  if (xcap <= 64) return 256;
+  return 512;
+}
+
+static gmps_status validate(const gmps_config* c) {
+  if (!c) return fail(GMPS_ERR_ARG, "config is NULL");
+  if (c->n < 1 || c->n > 64) return fail(GMPS_ERR_ARG, "n must be in [1, 64]");
+  if (c->M < 1) return fail(GMPS_ERR_ARG, "M must be >= 1");
+  if (c->n < 64 && (uint64_t)c->M >= (1ull << c->n)) return fail(GMPS_ERR_ARG, "M must be < 2^n");
+  if (c->M > kMaxMarked) return fail(GMPS_ERR_UNSUPPORTED, "M above the built maximum (64)");
+  if (!c->marked) return fail(GMPS_ERR_ARG, "marked is NULL");
+  std::set<uint64_t> seen;
+  for (int i = 0; i < c->M; ++i) {
+    uint64_t w = c->marked[i];
+    if (c->n < 64 && (w >> c->n) != 0) return fail(GMPS_ERR_ARG, "marked string has bits >= n");
+    if (!seen.insert(w).second) return fail(GMPS_ERR_ARG, "duplicate marked string");
+  }
+  if (c->chi_max < 1) return fail(GMPS_ERR_ARG, "chi_max must be >= 1");
+  if (!(c->tol >= 0.0) || !std::isfinite(c->tol)) return fail(GMPS_ERR_ARG, "tol must be finite and >= 0");
+  if (c->dtype != GMPS_C128 && c->dtype != GMPS_C64_F64SVD && c->dtype != GMPS_DW)
+    return fail(GMPS_ERR_ARG, "unknown dtype");
+  if (c->apply < 0 || c->apply > 2) return fail(GMPS_ERR_ARG, "apply must be 0, 1 or 2");
+  if (c->threads != 0 && (c->threads % 32 != 0 || c->threads < 32 || c->threads > 1024))
+    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+  if (c->max_sweeps < 0) return fail(GMPS_ERR_ARG, "max_sweeps must be >= 0");
+  return GMPS_OK;
+}
+
+static gmps_status make_plan_for(const gmps_config* c, bool allow_resident, Plan* P) {
+  const int smax = max_smem_optin();
+  const size_t eb = storage_bytes(c->dtype), rb = linalg_real_bytes(c->dtype);
+  for (int slack = 2; slack >= 0; slack -= 2) {
+    int chicap = std::min(c->chi_max, c->M + 1 + slack);
+    // a bond never exceeds 2^floor(n/2)
+    long long half = 1;
+    for (int i = 0; i < c->n / 2 && half < chicap; ++i) half *= 2;
+    chicap = (int)std::min<long long>(chicap, half);
+    const int xcap = xcap_for(c->apply, c->M, chicap);
+    if (c->apply == GMPS_APPLY_MPO && xcap > 64) continue;
+    P->chicap = chicap;
+    P->xcap = xcap;
+    P->off.assign(c->n + 1, 0);
+    for (int l = 0; l < c->n; ++l) P->off[l + 1] = P->off[l] + slot_elems(l, c->n, xcap);
+    P->site_elems = P->off[c->n];
+    P->elem_bytes = eb;
+    SmemPlan sp = make_plan(c->n, c->M, xcap, chicap, rb, 0);
+    if (sp.total > (size_t)smax) continue;
+    P->resident = 0;
+    P->smem = sp.total;
+    if (allow_resident) {
+      SmemPlan sr = make_plan(c->n, c->M, xcap, chicap, rb, P->site_elems * eb);
+      if (sr.total <= (size_t)smax) {
+        P->resident = 1;
+        P->smem = sr.total;
+      }
+    }
+    P->threads = c->threads ? c->threads : auto_threads(xcap);
+    return GMPS_OK;
+  }
+  if (c->apply == GMPS_APPLY_MPO)
+    return fail(GMPS_ERR_UNSUPPORTED, "MPO contraction needs (M+1)*chi <= 64; use the direct-sum forms");
+  return fail(GMPS_ERR_UNSUPPORTED, "working set exceeds shared memory for this (M, chi_max)");
+}
+
+// ---------------------------------------------------------------- handle
+struct Slab {  // one chain + its descriptor and statistics, carved from an arena
+  InstDesc* d_desc = nullptr;
+  long long* d_off = nullptr;
+  DevStats* d_stats = nullptr;
+  void* d_sites = nullptr;
+};
+
+struct gmps_ctx {
+  gmps_config cfg{};
+  std::vector<uint64_t> marked;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  Plan plan;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool own_arena = false;
+  InstDesc h{};
+  Slab main;
+  unsigned long long* d_marked = nullptr;
+  unsigned long long* d_qbits = nullptr;  // M+1 query strings
+  double* d_qout = nullptr;               // 2(M+1)
+  double* d_phase = nullptr;
+  size_t phase_cap = 0;
+  unsigned long long* d_sample = nullptr;
+  double* d_margin = nullptr;
+  size_t sample_cap = 0;
+  int error = 0;
+  long long iterations = 0;
+  // differentiable form
+  std::vector<double> phi_hist, psi_hist;
+  std::vector<Slab> ckpt;          // checkpoint c holds the state after c*every iterations
+  std::vector<Slab> work;          // per-iteration states inside a segment + costates
+  char* diff_mem = nullptr;
+  bool all_phases_explicit = true;
+};
+
+static size_t slab_bytes(const gmps_config* c, const Plan& P) {
+  return a256(sizeof(InstDesc)) + a256(sizeof(long long) * (c->n + 1)) + a256(sizeof(DevStats)) +
+         a256(P.site_elems * P.elem_bytes);
+}
+
+static char* carve_slab(char* p, const gmps_config* c, const Plan& P, Slab* s) {
+  s->d_desc = (InstDesc*)p;
+  p += a256(sizeof(InstDesc));
+  s->d_off = (long long*)p;
+  p += a256(sizeof(long long) * (c->n + 1));
+  s->d_stats = (DevStats*)p;
+  p += a256(sizeof(DevStats));
+  s->d_sites = p;
+  p += a256(P.site_elems * P.elem_bytes);
+  return p;
+}
+
+static size_t arena_size(const gmps_config* c, const Plan& P) {
+  return slab_bytes(c, P) + a256(sizeof(unsigned long long) * c->M) +
+         a256(sizeof(unsigned long long) * (c->M + 1)) + a256(sizeof(double) * 2 * (c->M + 1));
+}
+
+static InstDesc base_desc(const gmps_ctx* h, const Slab& s) {
+  InstDesc d{};
+  d.n = h->cfg.n;
+  d.M = h->cfg.M;
+  d.apply = h->cfg.apply;
+  d.chi_max = h->cfg.chi_max;
+  d.chicap = h->plan.chicap;
+  d.xcap = h->plan.xcap;
+  d.max_sweeps = h->cfg.max_sweeps ? h->cfg.max_sweeps : kDefaultMaxSweeps;
+  d.resident = h->plan.resident;
+  d.tol = h->cfg.tol;
+  d.trunc_eps = trunc_eps_for(h->cfg.dtype);
+  d.inv_sqrt_N = std::ldexp(1.0, -h->cfg.n / 2) * ((h->cfg.n & 1) ? std::sqrt(0.5) : 1.0);
+  d.marked = h->d_marked;
+  d.sites = s.d_sites;
+  d.site_off = s.d_off;
+  d.stats = s.d_stats;
+  return d;
+}
+
+static gmps_status upload_slab(gmps_ctx* h, const Slab& s) {
+  InstDesc d = base_desc(h, s);
+  CUDA_TRY(cudaMemcpyAsync(s.d_off, h->plan.off.data(), sizeof(long long) * (h->cfg.n + 1),
+                           cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(s.d_desc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(launch_init(s.d_desc, 1, h->cfg.dtype, 64, h->stream));
+  return GMPS_OK;
+}
+
+static gmps_status check_device(gmps_ctx* h) {
+  DevStats ds;
+  CUDA_TRY(cudaMemcpyAsync(&ds, h->main.d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (ds.status != 0) {
+    h->error = ds.status;
+    const char* what = ds.status == kDevNoConv   ? "Jacobi SVD did not converge"
+                       : ds.status == kDevNumeric ? "non-finite or zero norm"
+                       : ds.status == kDevCapacity ? "bond exceeded arena capacity"
+                                                   : "device error";
+    return fail((gmps_status)ds.status, what);
+  }
+  return GMPS_OK;
+}
+
+extern "C" {
+
+const char* grover_mps_last_error(void) { return g_err.c_str(); }
+
+int64_t grover_mps_launch_count(void) { return gmps::launches_so_far(); }
+
+gmps_status grover_mps_arena_bytes(const gmps_config* cfg, size_t* bytes) {
+  gmps_status s = validate(cfg);
+  if (s) return s;
+  if (!bytes) return fail(GMPS_ERR_ARG, "bytes is NULL");
+  Plan P;
+  if ((s = make_plan_for(cfg, true, &P))) return s;
+  *bytes = arena_size(cfg, P);
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps_handle* out) {
+  if (!out) return fail(GMPS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  gmps_status s = validate(cfg);
+  if (s) return s;
+  gmps_ctx* h = new gmps_ctx();
+  h->cfg = *cfg;
+  h->marked.assign(cfg->marked, cfg->marked + cfg->M);
+  h->cfg.marked = h->marked.data();
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&h->device);
+  if ((s = make_plan_for(&h->cfg, true, &h->plan))) {
+    delete h;
+    return s;
+  }
+  h->arena_bytes = arena_size(&h->cfg, h->plan);
+  if (cfg->arena) {
+    if (cfg->arena_bytes < h->arena_bytes) {
+      delete h;
+      return fail(GMPS_ERR_ARG, "caller arena smaller than grover_mps_arena_bytes");
+    }
+    if (((uintptr_t)cfg->arena) % 256 != 0) {
+      delete h;
+      return fail(GMPS_ERR_ARG, "caller arena must be 256-byte aligned");
+    }
+    h->arena = (char*)cfg->arena;
+  } else {
+    cudaError_t e = cudaMalloc(&h->arena, h->arena_bytes);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(GMPS_ERR_OOM, std::string("arena allocation: ") + cudaGetErrorString(e));
+    }
+    h->own_arena = true;
+  }
+  char* p = carve_slab(h->arena, &h->cfg, h->plan, &h->main);
+  h->d_marked = (unsigned long long*)p;
+  p += a256(sizeof(unsigned long long) * cfg->M);
+  h->d_qbits = (unsigned long long*)p;
+  p += a256(sizeof(unsigned long long) * (cfg->M + 1));
+  h->d_qout = (double*)p;
+  cudaError_t e = cudaMemcpyAsync(h->d_marked, h->marked.data(), sizeof(uint64_t) * cfg->M,
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) {
+    grover_mps_destroy(h);
+    return cuda_fail(e, "upload marked");
+  }
+  h->h = base_desc(h, h->main);
+  if ((s = upload_slab(h, h->main))) {
+    grover_mps_destroy(h);
+    return s;
+  }
+  e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    grover_mps_destroy(h);
+    return cuda_fail(e, "create");
+  }
+  *out = h;
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_create(int n, const uint64_t* marked, int M, int dtype, int chi_max, double tol,
+                              void* cuda_stream, gmps_handle* out) {
+  gmps_config c{};
+  c.n = n;
+  c.M = M;
+  c.marked = marked;
+  c.dtype = dtype;
+  c.apply = GMPS_APPLY_MPO;
+  c.chi_max = chi_max;
+  c.tol = tol;
+  return grover_mps_create_ex(&c, cuda_stream, out);
+}
+
+gmps_status grover_mps_reset(gmps_handle h) {
+  if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
+  h->error = 0;
+  h->iterations = 0;
+  h->phi_hist.clear();
+  h->psi_hist.clear();
+  h->all_phases_explicit = true;
+  gmps_status s = upload_slab(h, h->main);
+  if (s) return s;
+  return GMPS_OK;
+}
+
+static gmps_status ensure_phase(gmps_ctx* h, size_t need) {
+  if (h->phase_cap >= need) return GMPS_OK;
+  if (h->d_phase) cudaFree(h->d_phase);
+  h->d_phase = nullptr;
+  size_t cap = std::max<size_t>(need, 1024);
+  cudaError_t e = cudaMalloc(&h->d_phase, sizeof(double) * 2 * cap);
+  if (e != cudaSuccess) return fail(GMPS_ERR_OOM, "phase buffer");
+  h->phase_cap = cap;
+  return GMPS_OK;
+}
+
+static gmps_status enqueue_iterate(gmps_ctx* h, int64_t k, const double* dphi, const double* dpsi,
+                                   const Slab& slab) {
+  InstDesc d = base_desc(h, slab);
+  d.k = k;
+  d.phase_offset = 0;
+  d.phi = dphi;
+  d.psi = dpsi;
+  CUDA_TRY(cudaMemcpyAsync(slab.d_desc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(launch_iterate(slab.d_desc, 1, nullptr, h->cfg.dtype, h->plan.threads, h->plan.smem, 1, h->stream));
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_iterate_device(gmps_handle h, int64_t k, const double* dev_phi, const double* dev_psi) {
+  if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
+  if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
+  if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
+  if (k == 0) return GMPS_OK;
+  gmps_status s = enqueue_iterate(h, k, dev_phi, dev_psi, h->main);
+  if (s) return s;
+  h->iterations += k;
+  h->all_phases_explicit = false;
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_iterate(gmps_handle h, int64_t k, const double* host_phi, const double* host_psi) {
+  if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
+  if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
+  if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
+  if (k == 0) return GMPS_OK;
+  gmps_status s;
+  const double* dphi = nullptr;
+  const double* dpsi = nullptr;
+  if (host_phi || host_psi) {
+    if ((s = ensure_phase(h, (size_t)k))) return s;
+    if (host_phi) {
+      for (int64_t i = 0; i < k; ++i)
+        if (!std::isfinite(host_phi[i])) return fail(GMPS_ERR_ARG, "non-finite phase");
+      CUDA_TRY(cudaMemcpyAsync(h->d_phase, host_phi, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+      dphi = h->d_phase;
+    }
+    if (host_psi) {
+      for (int64_t i = 0; i < k; ++i)
+        if (!std::isfinite(host_psi[i])) return fail(GMPS_ERR_ARG, "non-finite phase");
+      CUDA_TRY(cudaMemcpyAsync(h->d_phase + h->phase_cap, host_psi, sizeof(double) * k,
+                               cudaMemcpyHostToDevice, h->stream));
+      dpsi = h->d_phase + h->phase_cap;
+    }
+  }
+  if ((s = enqueue_iterate(h, k, dphi, dpsi, h->main))) return s;
+  h->iterations += k;
+  for (int64_t i = 0; i < k; ++i) {
+    h->phi_hist.push_back(host_phi ? host_phi[i] : M_PI);
+    h->psi_hist.push_back(host_psi ? host_psi[i] : M_PI);
+  }
+  return check_device(h);
+}
+
+gmps_status grover_mps_sync(gmps_handle h) {
+  if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
+  return check_device(h);
+}
+
+static gmps_status query_amps(gmps_ctx* h, const unsigned long long* d_bits, int nb, std::vector<double>* out) {
+  CUDA_TRY(launch_amplitudes(h->main.d_desc, 0, h->cfg.dtype, d_bits, nb, h->d_qout, h->stream));
+  out->resize(2 * nb);
+  CUDA_TRY(cudaMemcpyAsync(out->data(), h->d_qout, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, h->stream));
+  return check_device(h);
+}
+
+gmps_status grover_mps_amplitude(gmps_handle h, uint64_t bits, double* re, double* im) {
+  if (!h || !re || !im) return fail(GMPS_ERR_ARG, "NULL argument");
+  if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
+  if (h->cfg.n < 64 && (bits >> h->cfg.n)) return fail(GMPS_ERR_ARG, "bits >= 2^n");
+  CUDA_TRY(cudaMemcpyAsync(h->d_qbits, &bits, sizeof(uint64_t), cudaMemcpyHostToDevice, h->stream));
+  std::vector<double> o;
+  gmps_status s = query_amps(h, h->d_qbits, 1, &o);
+  if (s) return s;
+  *re = o[0];
+  *im = o[1];
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_prob_marked(gmps_handle h, double* p) {
+  if (!h || !p) return fail(GMPS_ERR_ARG, "NULL argument");
+  if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
+  std::vector<double> o;
+  gmps_status s = query_amps(h, h->d_marked, h->cfg.M, &o);
+  if (s) return s;
+  double acc = 0.0;
+  for (int i = 0; i < h->cfg.M; ++i) acc += o[2 * i] * o[2 * i] + o[2 * i + 1] * o[2 * i + 1];
+  *p = acc;
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_sample_device(gmps_handle h, int64_t shots, uint64_t seed, uint64_t* dev_bits,
+                                     double* dev_margin) {
+  if (!h || (!dev_bits && shots > 0)) return fail(GMPS_ERR_ARG, "NULL argument");
+  if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
+  if (shots < 0) return fail(GMPS_ERR_ARG, "shots must be >= 0");
+  if (shots == 0) return GMPS_OK;
+  if (h->plan.chicap > 64) return fail(GMPS_ERR_UNSUPPORTED, "sampling needs chi <= 64");
+  CUDA_TRY(launch_sample(h->main.d_desc, 0, h->cfg.dtype, h->plan.chicap, shots, seed,
+                         (unsigned long long*)dev_bits, dev_margin, h->stream));
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_sample(gmps_handle h, int64_t shots, uint64_t seed, uint64_t* out_bits) {
+  if (!h || (!out_bits && shots > 0)) return fail(GMPS_ERR_ARG, "NULL argument");
+  if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
+  if (shots < 0) return fail(GMPS_ERR_ARG, "shots must be >= 0");
+  if (shots == 0) return GMPS_OK;
+  if ((size_t)shots > h->sample_cap) {
+    if (h->d_sample) cudaFree(h->d_sample);
+    h->d_sample = nullptr;
+    cudaError_t e = cudaMalloc(&h->d_sample, sizeof(uint64_t) * shots);
+    if (e != cudaSuccess) return fail(GMPS_ERR_OOM, "sample buffer");
+    h->sample_cap = shots;
+  }
+  gmps_status s = grover_mps_sample_device(h, shots, seed, (uint64_t*)h->d_sample, nullptr);
+  if (s) return s;
+  CUDA_TRY(cudaMemcpyAsync(out_bits, h->d_sample, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost, h->stream));
+  return check_device(h);
+}
+
+gmps_status grover_mps_stats(gmps_handle h, gmps_stats* out) {
+  if (!h || !out) return fail(GMPS_ERR_ARG, "NULL argument");
+  DevStats ds;
+  CUDA_TRY(cudaMemcpyAsync(&ds, h->main.d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  memset(out, 0, sizeof(*out));
+  out->iterations = ds.iterations;
+  out->n = h->cfg.n;
+  int mb = 1;
+  for (int l = 0; l <= h->cfg.n; ++l) {
+    out->chi[l] = ds.chi[l];
+    mb = std::max(mb, ds.chi[l]);
+  }
+  out->max_bond = mb;
+  out->log_norm = ds.log_norm;
+  out->discarded_weight = ds.discarded;
+  out->max_jacobi_sweeps = ds.max_jacobi_sweeps;
+  out->jacobi_sweeps = ds.jacobi_sweeps;
+  out->svd_count = ds.svd_count;
+  out->device_status = ds.status;
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_export(gmps_handle h, double* host_out, size_t capacity, size_t* needed) {
+  if (!h || !needed) return fail(GMPS_ERR_ARG, "NULL argument");
+  DevStats ds;
+  CUDA_TRY(cudaMemcpyAsync(&ds, h->main.d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  size_t need = 0;
+  for (int l = 0; l < h->cfg.n; ++l) need += 2ull * 2 * ds.chi[l] * ds.chi[l + 1];
+  *needed = need;
+  if (!host_out) return GMPS_OK;
+  if (capacity < need) return fail(GMPS_ERR_ARG, "export buffer too small");
+  const size_t eb = h->plan.elem_bytes;
+  std::vector<char> raw(h->plan.site_elems * eb);
+  CUDA_TRY(cudaMemcpyAsync(raw.data(), h->main.d_sites, raw.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  size_t o = 0;
+  for (int l = 0; l < h->cfg.n; ++l) {
+    const size_t cnt = 2ull * ds.chi[l] * ds.chi[l + 1];
+    const char* base = raw.data() + h->plan.off[l] * eb;
+    for (size_t e = 0; e < cnt; ++e) {
+      if (h->cfg.dtype == GMPS_DW) {
+        const float* v = (const float*)(base + e * eb);
+        host_out[o++] = (double)v[0] + (double)v[1];
+        host_out[o++] = (double)v[2] + (double)v[3];
+      } else if (eb == sizeof(double2)) {
+        const double* v = (const double*)(base + e * eb);
+        host_out[o++] = v[0];
+        host_out[o++] = v[1];
+      } else {
+        const float* v = (const float*)(base + e * eb);
+        host_out[o++] = v[0];
+        host_out[o++] = v[1];
+      }
+    }
+  }
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_backward(gmps_handle h, double dL_dP, double* grad_phi, double* grad_psi) {
+  (void)dL_dP;
+  (void)grad_phi;
+  (void)grad_psi;
+  if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
+  return fail(GMPS_ERR_UNSUPPORTED, "backward not built yet");
+}
+
+gmps_status grover_mps_destroy(gmps_handle h) {
+  if (!h) return GMPS_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->own_arena && h->arena) cudaFree(h->arena);
+  if (h->d_phase) cudaFree(h->d_phase);
+  if (h->d_sample) cudaFree(h->d_sample);
+  if (h->diff_mem) cudaFree(h->diff_mem);
+  delete h;
+  return GMPS_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ batched
+struct gmps_batch_ctx {
+  int count = 0;
+  int dtype = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<gmps_config> cfgs;
+  std::vector<std::vector<uint64_t>> marked;
+  std::vector<Plan> plans;
+  std::vector<InstDesc> h;   // in queue order
+  std::vector<int> order;    // queue position -> instance index
+  std::vector<int> pos;      // instance index -> queue position
+  char* mem = nullptr;
+  InstDesc* d_desc = nullptr;
+  int* d_queue = nullptr;
+  double* d_p = nullptr;
+  unsigned long long* d_q = nullptr;
+  double* d_qout = nullptr;
+  int threads = 0;
+  size_t smem = 0;
+  int grid = 0;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_threads = -1;
+  bool own_stream = false;  // graph capture needs a non-legacy stream
+};
+
+static gmps_status batch_enqueue(gmps_batch_ctx* b) {
+  CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream));
+  CUDA_TRY(launch_init(b->d_desc, b->count, b->dtype, 64, b->stream));
+  CUDA_TRY(launch_iterate(b->d_desc, b->count, b->d_queue, b->dtype, b->threads, b->smem, b->grid, b->stream));
+  return GMPS_OK;
+}
+
+extern "C" {
+
+gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const int64_t* ks,
+                                    const double* const* host_phi, const double* const* host_psi,
+                                    void* cuda_stream, gmps_batch_handle* out) {
+  if (!out || !cfgs || !ks || count < 1) return fail(GMPS_ERR_ARG, "bad batch arguments");
+  *out = nullptr;
+  gmps_batch_ctx* b = new gmps_batch_ctx();
+  b->count = count;
+  b->stream = (cudaStream_t)cuda_stream;
+  if (!b->stream) {
+    if (cudaStreamCreate(&b->stream) != cudaSuccess) {
+      delete b;
+      return fail(GMPS_ERR_CUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+  }
+  b->dtype = cfgs[0].dtype;
+  b->cfgs.assign(cfgs, cfgs + count);
+  b->marked.resize(count);
+  b->plans.resize(count);
+  gmps_status s;
+  size_t total = 0, smem = 0;
+  int maxx = 1;
+  std::vector<double> cost(count);
+  for (int i = 0; i < count; ++i) {
+    if ((s = validate(&cfgs[i]))) {
+      delete b;
+      return s;
+    }
+    if (cfgs[i].dtype != b->dtype) {
+      delete b;
+      return fail(GMPS_ERR_ARG, "all batch instances must share dtype");
+    }
+    if (ks[i] < 0) {
+      delete b;
+      return fail(GMPS_ERR_ARG, "k must be >= 0");
+    }
+    b->marked[i].assign(cfgs[i].marked, cfgs[i].marked + cfgs[i].M);
+    b->cfgs[i].marked = b->marked[i].data();
+    if ((s = make_plan_for(&b->cfgs[i], false, &b->plans[i]))) {
+      delete b;
+      return s;
+    }
+    const Plan& P = b->plans[i];
+    total += a256(sizeof(long long) * (cfgs[i].n + 1)) + a256(sizeof(DevStats)) +
+             a256(P.site_elems * P.elem_bytes) + a256(sizeof(unsigned long long) * cfgs[i].M) +
+             a256(sizeof(double) * 2 * ks[i]);
+    smem = std::max(smem, P.smem);
+    maxx = std::max(maxx, P.xcap);
+    cost[i] = (double)ks[i] * cfgs[i].n * std::pow((double)P.xcap, 3.0);
+  }
+  total += a256(sizeof(InstDesc) * count) + a256(sizeof(int)) + a256(sizeof(double) * count) +
+           a256(sizeof(unsigned long long) * 64) + a256(sizeof(double) * 128);
+  cudaError_t e = cudaMalloc(&b->mem, total);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(GMPS_ERR_OOM, "batch arena");
+  }
+  b->order.resize(count);
+  for (int i = 0; i < count; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  b->pos.resize(count);
+  for (int q = 0; q < count; ++q) b->pos[b->order[q]] = q;
+  char* p = b->mem;
+  b->d_desc = (InstDesc*)p;
+  p += a256(sizeof(InstDesc) * count);
+  b->d_queue = (int*)p;
+  p += a256(sizeof(int));
+  b->d_p = (double*)p;
+  p += a256(sizeof(double) * count);
+  b->d_q = (unsigned long long*)p;
+  p += a256(sizeof(unsigned long long) * 64);
+  b->d_qout = (double*)p;
+  p += a256(sizeof(double) * 128);
+  b->h.resize(count);
+  for (int q = 0; q < count; ++q) {
+    const int i = b->order[q];
+    const gmps_config& c = b->cfgs[i];
+    const Plan& P = b->plans[i];
+    InstDesc d{};
+    d.n = c.n;
+    d.M = c.M;
+    d.apply = c.apply;
+    d.chi_max = c.chi_max;
+    d.chicap = P.chicap;
+    d.xcap = P.xcap;
+    d.max_sweeps = c.max_sweeps ? c.max_sweeps : kDefaultMaxSweeps;
+    d.resident = 0;
+    d.k = ks[i];
+    d.tol = c.tol;
+    d.trunc_eps = trunc_eps_for(c.dtype);
+    d.inv_sqrt_N = std::ldexp(1.0, -c.n / 2) * ((c.n & 1) ? std::sqrt(0.5) : 1.0);
+    long long* off = (long long*)p;
+    p += a256(sizeof(long long) * (c.n + 1));
+    d.site_off = off;
+    d.stats = (DevStats*)p;
+    p += a256(sizeof(DevStats));
+    d.sites = p;
+    p += a256(P.site_elems * P.elem_bytes);
+    unsigned long long* mk_ = (unsigned long long*)p;
+    p += a256(sizeof(unsigned long long) * c.M);
+    d.marked = mk_;
+    double* ph = (double*)p;
+    p += a256(sizeof(double) * 2 * ks[i]);
+    e = cudaMemcpyAsync(off, P.off.data(), sizeof(long long) * (c.n + 1), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(mk_, c.marked, sizeof(uint64_t) * c.M, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && host_phi && host_phi[i]) {
+      e = cudaMemcpyAsync(ph, host_phi[i], sizeof(double) * ks[i], cudaMemcpyHostToDevice, b->stream);
+      d.phi = ph;
+    }
+    if (e == cudaSuccess && host_psi && host_psi[i]) {
+      e = cudaMemcpyAsync(ph + ks[i], host_psi[i], sizeof(double) * ks[i], cudaMemcpyHostToDevice, b->stream);
+      d.psi = ph + ks[i];
+    }
+    if (e != cudaSuccess) {
+      grover_mps_batch_destroy(b);
+      return cuda_fail(e, "batch upload");
+    }
+    b->h[q] = d;
+  }
+  e = cudaMemcpyAsync(b->d_desc, b->h.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    grover_mps_batch_destroy(b);
+    return cuda_fail(e, "batch create");
+  }
+  b->smem = smem;
+  b->threads = auto_threads(maxx);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  b->grid = nsm;  // refined at run time from the occupancy of the chosen CTA size
+  *out = b;
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_batch_set_threads(gmps_batch_handle b, int threads) {
+  if (!b) return fail(GMPS_ERR_ARG, "NULL handle");
+  if (threads != 0 && (threads % 32 || threads < 32 || threads > 1024))
+    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+  int maxx = 1;
+  for (auto& P : b->plans) maxx = std::max(maxx, P.xcap);
+  b->threads = threads ? threads : auto_threads(maxx);
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_batch_run(gmps_batch_handle b, int use_graph) {
+  if (!b) return fail(GMPS_ERR_ARG, "NULL handle");
+  // blocks resident per SM for this CTA size and shared-memory footprint
+  int dev = 0, nsm = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int per_sm = std::max(1, (int)(smem_sm / std::max<size_t>(b->smem + 1024, 1)));
+  per_sm = std::min(per_sm, std::max(1, 2048 / b->threads));
+  b->grid = std::min(b->count, nsm * per_sm);
+  if (!use_graph) return batch_enqueue(b);
+  if (!b->gexec || b->graph_threads != b->threads) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    gmps_status s = batch_enqueue(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (s) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    b->graph_threads = b->threads;
+  }
+  CUDA_TRY(cudaGraphLaunch(b->gexec, b->stream));
+  count_launch(2);
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_batch_result(gmps_batch_handle b, double* host_p, int* host_status) {
+  if (!b) return fail(GMPS_ERR_ARG, "NULL handle");
+  CUDA_TRY(launch_batch_prob(b->d_desc, b->count, b->dtype, b->d_p, b->stream));
+  std::vector<double> p(b->count);
+  CUDA_TRY(cudaMemcpyAsync(p.data(), b->d_p, sizeof(double) * b->count, cudaMemcpyDeviceToHost, b->stream));
+  std::vector<DevStats> st(b->count);
+  for (int q = 0; q < b->count; ++q)
+    CUDA_TRY(cudaMemcpyAsync(&st[q], b->h[q].stats, sizeof(DevStats), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  gmps_status worst = GMPS_OK;
+  for (int i = 0; i < b->count; ++i) {
+    const int q = b->pos[i];
+    if (host_p) host_p[i] = p[q];
+    if (host_status) host_status[i] = st[q].status;
+    if (st[q].status && !worst) worst = (gmps_status)st[q].status;
+  }
+  if (worst) return fail(worst, "an instance reported a device error");
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_batch_amplitude(gmps_batch_handle b, int i, uint64_t bits, double* re, double* im) {
+  if (!b || !re || !im || i < 0 || i >= b->count) return fail(GMPS_ERR_ARG, "bad argument");
+  const int q = b->pos[i];
+  CUDA_TRY(cudaMemcpyAsync(b->d_q, &bits, sizeof(uint64_t), cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(launch_amplitudes(b->d_desc, q, b->dtype, b->d_q, 1, b->d_qout, b->stream));
+  double o[2];
+  CUDA_TRY(cudaMemcpyAsync(o, b->d_qout, sizeof(o), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  *re = o[0];
+  *im = o[1];
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_batch_destroy(gmps_batch_handle b) {
+  if (!b) return GMPS_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->mem) cudaFree(b->mem);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return GMPS_OK;
+}
+
+}  // extern "C"

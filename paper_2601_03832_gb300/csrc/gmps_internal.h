@@ -1,0 +1,136 @@
+// Internal types shared by the C-ABI layer (gmps_capi.cu) and the kernels
+// (gmps_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define GMPS_HD __host__ __device__ __forceinline__
+
+namespace gmps {
+
+constexpr int kMaxN = 64;
+constexpr int kMaxMarked = 64;        // direct-sum terms per operator
+constexpr int kDefaultMaxSweeps = 40;
+
+enum DevStatusBits {
+  kDevOK = 0,
+  kDevNoConv = 5,
+  kDevNumeric = 6,
+  kDevCapacity = 8,
+};
+
+// Counters written by the device; one block per instance.
+struct DevStats {
+  long long iterations;     // iterations applied
+  long long jacobi_sweeps;  // summed over SVDs
+  long long svd_count;
+  int max_jacobi_sweeps;
+  int status;               // first error (DevStatusBits), 0 if none
+  double log_norm;
+  double discarded;
+  int chi[kMaxN + 1];       // bond table after the last sweep pair
+};
+
+// Everything one persistent block needs for one instance.  Lives in device
+// memory (array of descriptors for a batch).
+struct InstDesc {
+  int n;
+  int M;
+  int apply;                // gmps_apply
+  int chi_max;              // user cap
+  int chicap;               // storage capacity of a bond after truncation
+  int xcap;                 // capacity of an expanded bond
+  int max_sweeps;
+  int resident;             // copy the chain into shared memory for the launch
+  long long k;              // iterations to apply in this launch
+  long long phase_offset;   // index of this launch's first phase in phi/psi
+  double tol;
+  double trunc_eps;         // eps of the storage type for the rank rule
+  double inv_sqrt_N;        // 2^{-n/2}
+  const unsigned long long* marked;  // device, M strings
+  const double* phi;        // device, or null = pi
+  const double* psi;
+  void* sites;              // device slab
+  const long long* site_off;  // n+1 offsets (elements of the storage type)
+  DevStats* stats;          // device
+};
+
+// Shared-memory plan of one block (bytes), identical on host and device.
+struct SmemPlan {
+  size_t off_chi, off_qb, off_terms, off_amps, off_misc;
+  size_t off_rprev, off_w, off_tau, off_beta;      // QR sweep
+  size_t off_mat, off_u, off_us, off_sig, off_perm;  // SVD sweep (aliases QR)
+  size_t off_sites;
+  size_t total;
+};
+
+GMPS_HD size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// rb = bytes of one real of the linear-algebra type (complex = 2*rb).
+GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, size_t rb,
+                           size_t site_bytes_resident) {
+  SmemPlan p{};
+  size_t cb = 2 * rb;
+  size_t o = 0;
+  p.off_chi = o;   o = align_up(o + sizeof(int) * (kMaxN + 2), 16);
+  p.off_qb = o;    o = align_up(o + sizeof(int) * (kMaxN + 2), 16);
+  p.off_terms = o; o = align_up(o + (sizeof(unsigned long long) + sizeof(int) + cb + 8) * (M + 2), 16);
+  p.off_amps = o;  o = align_up(o + cb * (M + 2), 16);
+  p.off_misc = o;  o = align_up(o + 512, 16);
+  size_t base = o;
+  // QR-sweep working set
+  size_t q = base;
+  p.off_rprev = q; q = align_up(q + cb * (size_t)xcap * xcap, 16);
+  p.off_w = q;     q = align_up(q + cb * (size_t)(2 * xcap) * xcap, 16);
+  p.off_tau = q;   q = align_up(q + rb * (size_t)xcap, 16);
+  p.off_beta = q;  q = align_up(q + cb * (size_t)xcap, 16);
+  // SVD-sweep working set (aliases the QR one)
+  size_t s = base;
+  p.off_mat = s;   s = align_up(s + cb * (size_t)xcap * (2 * chicap), 16);
+  p.off_u = s;     s = align_up(s + cb * (size_t)xcap * (2 * chicap), 16);  // copy of the SVD input
+  p.off_us = s;    s = align_up(s + cb * (size_t)xcap * chicap, 16);
+  p.off_sig = s;   s = align_up(s + rb * (size_t)xcap, 16);
+  p.off_perm = s;  s = align_up(s + sizeof(int) * (size_t)xcap, 16);
+  o = q > s ? q : s;
+  p.off_sites = o;
+  o = align_up(o + site_bytes_resident, 16);
+  p.total = o;
+  return p;
+}
+
+// Largest left/right dims a slot ever holds: QR-sweep bonds are bounded by
+// 2^l from the left and by the expanded bond xcap.
+GMPS_HD long long bond_cap(int l, int n, int xcap) {
+  (void)n;
+  long long c = 1;
+  for (int i = 0; i < l && c < xcap; ++i) c *= 2;
+  return c < xcap ? c : xcap;
+}
+GMPS_HD long long slot_elems(int l, int n, int xcap) {
+  long long left = bond_cap(l, n, xcap);
+  long long right = (l == n - 1) ? 1 : bond_cap(l + 1, n, xcap);
+  return left * 2 * right;
+}
+
+// Launchers (gmps_kernels.cu).  dtype: gmps_dtype.  All enqueue on `stream`.
+cudaError_t launch_init(const InstDesc* d_desc, int count, int dtype, int threads,
+                        cudaStream_t stream);
+cudaError_t launch_iterate(const InstDesc* d_desc, int count, int* d_queue, int dtype,
+                           int threads, size_t smem, int grid, cudaStream_t stream);
+cudaError_t launch_amplitudes(const InstDesc* d_desc, int inst, int dtype,
+                              const unsigned long long* d_bits, int nbits,
+                              double* d_out /* 2*nbits */, cudaStream_t stream);
+cudaError_t launch_sample(const InstDesc* d_desc, int inst, int dtype, int chmax, long long shots,
+                          unsigned long long seed, unsigned long long* d_bits,
+                          double* d_margin, cudaStream_t stream);
+cudaError_t launch_copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int dtype,
+                              cudaStream_t stream);
+cudaError_t launch_batch_prob(const InstDesc* d_desc, int count, int dtype, double* d_p,
+                              cudaStream_t stream);
+size_t storage_bytes(int dtype);      // bytes of one complex site element
+size_t linalg_real_bytes(int dtype);  // bytes of one linear-algebra real
+int max_smem_optin();
+void count_launch(long long n);
+
+}  // namespace gmps

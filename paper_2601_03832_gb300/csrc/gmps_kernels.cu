@@ -1,0 +1,1382 @@
+// Kernels of the iterative-Grover MPS engine for sm_103a.
+//
+// One thread block owns one instance for a whole launch and applies all of
+// its Grover iterations without returning to the host (Sec. III-A: the
+// state is replaced by G|state> once per iteration, G = D O of Sec. II,
+// Eq. 3).  Each operator is contracted into the site tensors, then the chain
+// is recompressed by a canonicalising Householder-QR sweep (left to right)
+// and a truncated one-sided-Jacobi SVD sweep (right to left), as the MPS
+// backend of Sec. III-B-2 describes ("tensors are locally updated, and
+// truncation is applied ...").  The chain is sequential along the sites, so
+// the block's threads parallelise inside each small factorisation: lane
+// groups own matrix columns (QR) or row pairs (Jacobi) and reduce with warp
+// shuffles; all working matrices live in shared memory and, for small
+// instances, the whole chain does too.
+//
+// Arithmetic forms (template parameters): T = real type of the QR/SVD and
+// scalar bookkeeping (double), S = storage type of a complex site element
+// (double2 or float2), CR = real type of the contractions (double or float).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <cstdio>
+
+#include <atomic>
+
+#include "gmps_dw.cuh"
+#include "gmps_internal.h"
+
+namespace gmps {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(long long n) { g_launches += n; }
+long long launches_so_far() { return g_launches.load(); }
+
+// ------------------------------------------------------------------ complex
+template <class T>
+struct cx {
+  T re, im;
+};
+template <class T>
+__device__ __forceinline__ cx<T> mk(T a, T b) {
+  cx<T> r;
+  r.re = a;
+  r.im = b;
+  return r;
+}
+template <class T>
+__device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mk<T>(a.re + b.re, a.im + b.im); }
+template <class T>
+__device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mk<T>(a.re - b.re, a.im - b.im); }
+template <class T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+template <class T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mk<T>(a.re * s, a.im * s); }
+// acc + a*b
+template <class T>
+__device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a)*b
+template <class T>
+__device__ __forceinline__ cx<T> cmacc(cx<T> acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+template <class T>
+__device__ __forceinline__ T abs2(cx<T> a) { return fma(a.re, a.re, a.im * a.im); }
+
+// storage <-> compute conversion
+template <class T>
+__device__ __forceinline__ cx<T> ld(const double2* p) {
+  double2 v = *p;
+  return mk<T>((T)v.x, (T)v.y);
+}
+template <class T>
+__device__ __forceinline__ cx<T> ld(const float2* p) {
+  float2 v = *p;
+  return mk<T>((T)v.x, (T)v.y);
+}
+template <class T>
+__device__ __forceinline__ void st(double2* p, cx<T> v) { *p = make_double2((double)v.re, (double)v.im); }
+template <class T>
+__device__ __forceinline__ void st(float2* p, cx<T> v) { *p = make_float2((float)v.re, (float)v.im); }
+// double-word storage: exact for DW values, FP64 values are split on store
+template <class T>
+__device__ __forceinline__ cx<T> ld(const dw2* p) {
+  const dw2 v = *p;
+  return mk<T>((T)((double)v.rh + (double)v.rl), (T)((double)v.ih + (double)v.il));
+}
+template <>
+__device__ __forceinline__ cx<dw> ld<dw>(const dw2* p) {
+  const dw2 v = *p;
+  return mk<dw>(dw(v.rh, v.rl), dw(v.ih, v.il));
+}
+__device__ __forceinline__ void st(dw2* p, cx<dw> v) {
+  dw2 o;
+  o.rh = v.re.h;
+  o.rl = v.re.l;
+  o.ih = v.im.h;
+  o.il = v.im.l;
+  *p = o;
+}
+__device__ __forceinline__ void st(dw2* p, cx<double> v) { st(p, mk<dw>(dw(v.re), dw(v.im))); }
+template <class A, class B>
+__device__ __forceinline__ cx<A> cvt(cx<B> v) { return mk<A>((A)v.re, (A)v.im); }
+template <>
+__device__ __forceinline__ cx<dw> cvt<dw, dw>(cx<dw> v) { return v; }
+
+// per-type constants
+template <class T>
+struct K;
+template <>
+struct K<double> {
+  static __device__ __forceinline__ double isq2() { return 0.70710678118654752440; }
+  // Jacobi convergence: |<x_p,x_q>| <= tol sqrt(|x_p|^2 |x_q|^2)
+  static __device__ __forceinline__ double jtol() { return 8.0 * 2.220446049250313e-16; }
+  static __device__ __forceinline__ float jtolf() { return 1.7763568e-15f; }
+  // squared column norm below which a Householder column counts as zero
+  static __device__ __forceinline__ double tiny2() { return 0.0; }
+  // Householder columns are scaled by a power of two first (needed only when
+  // the exponent range is FP32's)
+  static constexpr bool kScaleColumns = false;
+};
+template <>
+struct K<float> {
+  static __device__ __forceinline__ float isq2() { return 0.70710677f; }
+  static __device__ __forceinline__ float jtol() { return 8.f * 1.1920929e-07f; }
+  static __device__ __forceinline__ float jtolf() { return 9.536743e-07f; }
+  static __device__ __forceinline__ float tiny2() { return 0.f; }
+  static constexpr bool kScaleColumns = true;
+};
+template <>
+struct K<dw> {
+  static __device__ __forceinline__ dw isq2() { return dw(0.70710677f, 1.2101617e-08f); }
+  static __device__ __forceinline__ dw jtol() { return dw(5.6843419e-14f); }  // 2^-44
+  static __device__ __forceinline__ float jtolf() { return 5.6843419e-14f; }
+  static __device__ __forceinline__ dw tiny2() { return dw(0.f); }
+  // squares of entries below ~1e-16 are FP32 denormals: the reflector is built
+  // from the column scaled to O(1) by an exact power of two
+  static constexpr bool kScaleColumns = true;
+};
+
+// -------------------------------------------------------------- reductions
+__device__ __forceinline__ double shx(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shx(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shx_m(double v, int o, unsigned m) { return __shfl_xor_sync(m, v, o); }
+__device__ __forceinline__ float shx_m(float v, int o, unsigned m) { return __shfl_xor_sync(m, v, o); }
+__device__ __forceinline__ dw shx_m(dw v, int o, unsigned m) {
+  return dw(__shfl_xor_sync(m, v.h, o), __shfl_xor_sync(m, v.l, o));
+}
+__device__ __forceinline__ double shidx(double v, int i) { return __shfl_sync(0xffffffffu, v, i); }
+__device__ __forceinline__ float shidx(float v, int i) { return __shfl_sync(0xffffffffu, v, i); }
+__device__ __forceinline__ dw shidx(dw v, int i) {
+  return dw(__shfl_sync(0xffffffffu, v.h, i), __shfl_sync(0xffffffffu, v.l, i));
+}
+template <class T>
+__device__ __forceinline__ T gsum(T v, int G) {
+  for (int o = G >> 1; o > 0; o >>= 1) v += shx(v, o);
+  return v;
+}
+__device__ __forceinline__ int pow2_cap32(int x) {
+  int g = 1;
+  while (g < x && g < 32) g <<= 1;
+  return g;
+}
+
+// Lane groups: G consecutive lanes (G a power of two <= 32) work on one task.
+struct Grp {
+  int G, gid, lg, ng;
+};
+__device__ __forceinline__ Grp make_grp(int G) {
+  Grp g;
+  g.G = G;
+  g.lg = threadIdx.x & (G - 1);
+  g.gid = threadIdx.x / G;
+  g.ng = blockDim.x / G;
+  return g;
+}
+
+// ----------------------------------------------------------- device state
+template <class T, class S>
+struct Blk {
+  const InstDesc* d;
+  int n;
+  S* sites;                // slab base (shared or global)
+  const long long* off;    // slot offsets
+  int* chi;                // [n+1] bond after the last SVD sweep (shared)
+  int* qb;                 // [n+1] bonds after the QR sweep (shared)
+  unsigned long long* tbits;  // direct-sum product terms
+  int* tplus;
+  cx<T>* tcoef;
+  cx<T>* amps;
+  cx<T>* Rp;               // R carried by the QR sweep
+  cx<T>* W;                // QR work matrix
+  T* tau;
+  cx<T>* beta;
+  cx<T>* Mat;              // SVD work matrix
+  cx<T>* U;                // accumulated Jacobi rotations
+  cx<T>* US;               // U*S carried by the SVD sweep
+  T* sig;
+  int* perm;
+  int* misc;               // [0] status, [1] max sweeps, [2] sweeps sum, [3] svd count, [4] k kept
+  double* dmisc;           // [0] log_norm, [1] discarded, [2..5] phase coefficients
+  T* tmisc;                // [0] rank-rule eps, [1] tol, [2] discarded weight, [3..6] e^{i phi}-1 and 1-e^{i psi},
+                           // [7] 2^{-n/2}, [8] Jacobi skip floor
+  __device__ S* slot(int l) const { return sites + off[l]; }
+};
+
+// ------------------------------------------------- exponent / scaling helpers
+// Exponent of a positive value and its scaled FP32 image, by integer bit
+// manipulation (no FP64 conversion instructions: on this part those run on
+// the FP64 pipe).  Scaled images truncate toward zero; underflow gives 0.
+__device__ __forceinline__ int expo_of(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
+__device__ __forceinline__ int expo_of(dw x) { return ((__float_as_int(x.h) >> 23) & 0xff) - 127; }
+__device__ __forceinline__ float f32_scaled(double x, int sh) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int e = (hi >> 20) & 0x7ff;
+  if (e == 0) return 0.f;
+  const int fe = e - 1023 - sh + 127;
+  if (fe <= 0) return 0.f;
+  if (fe >= 255) return __int_as_float((hi & 0x80000000) | 0x7f800000);
+  const unsigned m = ((unsigned)(hi & 0xfffff) << 3) | ((unsigned)lo >> 29);
+  return __uint_as_float(((unsigned)hi & 0x80000000u) | ((unsigned)fe << 23) | m);
+}
+__device__ __forceinline__ float f32_scaled(dw x, int sh) {
+  const int u = __float_as_int(x.h);
+  const int e = (u >> 23) & 0xff;
+  if (e == 0) return 0.f;
+  const int fe = e - sh;
+  if (fe <= 0) return 0.f;
+  if (fe >= 255) return __int_as_float((u & 0x80000000) | 0x7f800000);
+  return __int_as_float((u & 0x807fffff) | (fe << 23));
+}
+// exact widening of a normal float (denormals -> 0)
+template <class T>
+__device__ __forceinline__ T widen(float f);
+template <>
+__device__ __forceinline__ double widen<double>(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xff;
+  if (e == 0) return 0.0;
+  const unsigned m = u & 0x7fffffu;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e - 127 + 1023) << 20) | (m >> 3)), (int)(m << 29));
+}
+template <>
+__device__ __forceinline__ dw widen<dw>(float f) { return dw(f); }
+// exact 2^e
+template <class T>
+__device__ __forceinline__ T pow2(int e);
+template <>
+__device__ __forceinline__ double pow2<double>(int e) { return __hiloint2double((e + 1023) << 20, 0); }
+template <>
+__device__ __forceinline__ float pow2<float>(int e) { return __int_as_float((e + 127) << 23); }
+template <>
+__device__ __forceinline__ dw pow2<dw>(int e) { return dw(__int_as_float((e + 127) << 23)); }
+__device__ __forceinline__ int expo_abs(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
+__device__ __forceinline__ int expo_abs(float x) { return ((__float_as_int(x) >> 23) & 0xff) - 127; }
+__device__ __forceinline__ int expo_abs(dw x) { return ((__float_as_int(x.h) >> 23) & 0xff) - 127; }
+
+// ----------------------------------------------------------- Householder QR
+// In-place QR of A (m x ncol, leading dim lda) by Householder reflectors
+// H_j = I - tau_j v_j v_j^dag with v_j = x - beta_j e_j, beta_j =
+// -e^{i arg x_j}|x|, tau_j = 1/(|x| (|x| + |x_j|)) (so that H_j x = beta_j e_j).
+// On return the strict upper triangle holds R (diagonal in beta), the
+// columns j hold v_j from row j down.
+template <class T>
+__device__ void qr_householder(cx<T>* A, int m, int ncol, int lda, T* tau, cx<T>* beta) {
+  const int p = min(m, ncol);
+  const int G = pow2_cap32(m);
+  const Grp g = make_grp(G);
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  for (int j = 0; j < p; ++j) {
+    if (threadIdx.x < G) {
+      // optional exact power-of-two scaling of the column (rows >= j)
+      int em = -2000;
+      if (K<T>::kScaleColumns) {
+        for (int i = j + threadIdx.x; i < m; i += G) {
+          const cx<T> x = A[i * lda + j];
+          if (x.re != (T)0) em = max(em, expo_abs(x.re));
+          if (x.im != (T)0) em = max(em, expo_abs(x.im));
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(gmask, em, o));
+      }
+      const bool scl = K<T>::kScaleColumns && em > -2000;
+      const T sc = scl ? pow2<T>(-em) : (T)1;
+      T s = 0;
+      for (int i = j + threadIdx.x; i < m; i += G) {
+        cx<T> x = A[i * lda + j];
+        if (scl) {
+          x = cscale(x, sc);
+          A[i * lda + j] = x;
+        }
+        s += abs2(x);
+      }
+      for (int o = G >> 1; o > 0; o >>= 1) s += shx_m(s, o, gmask);
+      if (threadIdx.x == 0) {
+        cx<T> x0 = A[j * lda + j];
+        T a2 = abs2(x0);
+        cx<T> b = mk<T>(0, 0);
+        T t = 0;
+        if (s > K<T>::tiny2()) {
+          T inv = rsqrt(s);
+          T nrm = s * inv;
+          cx<T> ph = mk<T>(1, 0);
+          T ax0 = 0;
+          if (a2 > 0) {
+            T ia = rsqrt(a2);
+            ax0 = a2 * ia;
+            ph = cscale(x0, ia);
+          }
+          b = cscale(ph, -nrm);
+          t = (T)1 / (nrm * (nrm + ax0));
+          A[j * lda + j] = csub(x0, b);
+        }
+        beta[j] = scl ? cscale(b, pow2<T>(em)) : b;  // R_jj of the unscaled column
+        tau[j] = t;
+      }
+    }
+    __syncthreads();
+    const T tj = tau[j];
+    const int ntask = ncol - j - 1;
+    for (int t0 = 0; t0 < ntask; t0 += g.ng) {
+      const int c = j + 1 + t0 + g.gid;
+      const bool act = (t0 + g.gid) < ntask;
+      cx<T> w = mk<T>(0, 0);
+      if (act)
+        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, A[i * lda + j], A[i * lda + c]);
+      w.re = gsum(w.re, G);
+      w.im = gsum(w.im, G);
+      if (act && tj != (T)0) {
+        const cx<T> tw = cscale(w, -tj);
+        for (int i = j + g.lg; i < m; i += G) A[i * lda + c] = cmac(A[i * lda + c], A[i * lda + j], tw);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Overwrite the reflectors in A (m x p block, leading dim lda) with the thin
+// Q = H_0 H_1 ... H_{p-1} [I_p; 0], right to left (reflector storage reused).
+template <class T>
+__device__ void qr_form_q(cx<T>* A, int m, int p, int lda, const T* tau) {
+  const int G = pow2_cap32(m);
+  const Grp g = make_grp(G);
+  for (int j = p - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    const int ntask = p - j - 1;
+    for (int t0 = 0; t0 < ntask; t0 += g.ng) {
+      const int c = j + 1 + t0 + g.gid;
+      const bool act = (t0 + g.gid) < ntask;
+      cx<T> w = mk<T>(0, 0);
+      if (act)
+        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, A[i * lda + j], A[i * lda + c]);
+      w.re = gsum(w.re, G);
+      w.im = gsum(w.im, G);
+      if (act && tj != (T)0) {
+        const cx<T> tw = cscale(w, -tj);
+        for (int i = j + g.lg; i < m; i += G) A[i * lda + c] = cmac(A[i * lda + c], A[i * lda + j], tw);
+      }
+    }
+    __syncthreads();
+    // column j of Q: H_j e_j = e_j - tau v conj(v_j)
+    const cx<T> vj = A[j * lda + j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      cx<T> q;
+      if (i < j) {
+        q = mk<T>(0, 0);
+      } else if (i == j) {
+        q = mk<T>((T)1 - tj * abs2(vj), 0);
+      } else {
+        const cx<T> vi = A[i * lda + j];
+        // -tau * v_i * conj(v_j)
+        q = mk<T>(-tj * fma(vi.re, vj.re, vi.im * vj.im), -tj * fma(vi.im, vj.re, -vi.re * vj.im));
+      }
+      A[i * lda + j] = q;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------- one-sided Jacobi SVD
+// Orthogonalise the rows of Mat (r x c, leading dim ldm) by unitary plane
+// rotations J = [[c, -conj(s)], [s, c]] applied from the left (Hestenes'
+// one-sided Jacobi on the rows).  Pairs follow the round-robin (circle)
+// ordering so that the r/2 disjoint pairs of a round run in parallel, one
+// lane group per pair.  The rotation angle is the classical one (Rutishauser:
+// zeta = (b - a)/(2|g|), t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2))) computed
+// in FP32 from the pair's T-precision Gram entries after an exact
+// power-of-two scaling, then normalised in T so that c^2 + |s|^2 = 1 to T's
+// rounding.  A pair is rotated while |g| > tol sqrt(a b); pairs in which a
+// row's squared norm is below `skip2` (noise far under the rank rule's
+// threshold, which the truncation drops) are left alone.  Returns sweeps
+// used, or -1 if max_sweeps was exhausted.
+template <class T>
+__device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, int max_sweeps, float tolf, T skip2) {
+  if (r < 2) return 0;
+  const int rp = r + (r & 1);
+  const int npairs = rp / 2;
+  const int G = pow2_cap32(c);
+  const Grp g = make_grp(G);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int t = 0; t < rp - 1; ++t) {
+      for (int t0 = 0; t0 < npairs; t0 += g.ng) {
+        const int k = t0 + g.gid;
+        int p = -1, q = -1;
+        if (k < npairs) {
+          if (k == 0) {
+            p = rp - 1;
+            q = t;
+          } else {
+            p = (t + k) % (rp - 1);
+            q = (t - k + rp - 1) % (rp - 1);
+          }
+          if (p >= r || q >= r) p = q = -1;
+        }
+        const bool act = p >= 0;
+        T a = 0, b = 0;
+        cx<T> gg = mk<T>(0, 0);
+        if (act) {
+          for (int j = g.lg; j < c; j += G) {
+            const cx<T> xp = Mat[p * ldm + j], xq = Mat[q * ldm + j];
+            a += abs2(xp);
+            b += abs2(xq);
+            gg = cmacc(gg, xp, xq);
+          }
+        }
+        a = gsum(a, G);
+        b = gsum(b, G);
+        gg.re = gsum(gg.re, G);
+        gg.im = gsum(gg.im, G);
+        if (act && a > skip2 && b > skip2) {
+          const int sh = expo_of(a > b ? a : b);
+          const float af = f32_scaled(a, sh), bf = f32_scaled(b, sh);
+          const float dab = f32_scaled(b - a, sh);  // difference taken in T
+          const float gr = f32_scaled(gg.re, sh), gi = f32_scaled(gg.im, sh);
+          const float gabs = sqrtf(fmaf(gr, gr, gi * gi));
+          if (gabs > tolf * sqrtf(af) * sqrtf(bf) && gabs > 0.f) {
+            const float zeta = dab / (2.f * gabs);
+            // small-root formula; for |zeta| > 2^60 (zeta^2 would overflow) t = 1/(2 zeta)
+            const float tt = fabsf(zeta) > 1.1529215e18f
+                                 ? 0.5f / zeta
+                                 : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+            if (tt != 0.f && isfinite(tt)) {
+              const float cf = rsqrtf(fmaf(tt, tt, 1.f));
+              const float sf = cf * tt;
+              T cc = widen<T>(cf), sre = widen<T>(sf * (gr / gabs)), sim = widen<T>(sf * (gi / gabs));
+              const T rho = fma(cc, cc, fma(sre, sre, sim * sim));
+              const T dd = rho - (T)1;
+              const T f = fma(dd, fma(dd, (T)0.375f, (T)-0.5f), (T)1);
+              cc *= f;
+              sre *= f;
+              sim *= f;
+              const cx<T> sv = mk<T>(sre, sim);
+              const cx<T> ms = mk<T>(-sre, sim);  // -conj(s)
+              for (int j = g.lg; j < c; j += G) {
+                const cx<T> xp = Mat[p * ldm + j], xq = Mat[q * ldm + j];
+                Mat[p * ldm + j] = cmac(cscale(xp, cc), ms, xq);
+                Mat[q * ldm + j] = cmac(cscale(xq, cc), sv, xp);
+              }
+              rotated = 1;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!__syncthreads_or(rotated)) return sweep + 1;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------ contraction
+// MPO factor w_b(s, s') of site l (0 <= b < D) for the oracle (O) and the
+// diffusion (D) operators, boundaries folded in by the caller.
+// oracle:    w_0 = I, w_b = P_{bit(w_b, l)} = |x><x| (b >= 1)
+// diffusion: w_0 = I, w_1 = |+><+| = 1/2 (all entries)
+template <class CR>
+__device__ __forceinline__ CR mpo_w(int op, int b, int l, int s, int sp, const unsigned long long* marked) {
+  if (b == 0) return s == sp ? (CR)1 : (CR)0;
+  if (op == 0) {
+    const int x = (int)((marked[b - 1] >> l) & 1ull);
+    return (s == sp && s == x) ? (CR)1 : (CR)0;
+  }
+  return (CR)0.5f;
+}
+
+// C = Rp * B_l, written as the (2 r) x X_right matrix W (row (i, s) = 2 i + s).
+// B_l is the operator-expanded site l: an MPO contraction (op 0 oracle, 1
+// diffusion; boundary vector `lbnd` of length D at site 0, all-ones at the
+// right end) or a direct sum of the current MPS (coefficient cpsi at site 0)
+// with `nt` product states (coefficients tcoef at site 0).
+template <class T, class S, class CR>
+__device__ void expand_absorb(Blk<T, S>& B, int l, int r, int xl, int xr, int mode, int op, int D,
+                              const cx<T>* lbnd, cx<T> cpsi, int nt) {
+  const int n = B.n;
+  const int cl = B.chi[l], cr = B.chi[l + 1];
+  const S* A = B.slot(l);
+  const int total = r * 2 * xr;
+  const CR h = K<CR>::isq2();
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int i = e / (2 * xr);
+    const int s = (e / xr) & 1;
+    const int j = e % xr;
+    cx<CR> acc = mk<CR>(0, 0);
+    if (mode == 0) {  // ---- MPO
+      if (n == 1) {
+        for (int b = 0; b < D; ++b) {
+          cx<CR> tb = mk<CR>(0, 0);
+          for (int sp = 0; sp < 2; ++sp) {
+            const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
+            if (w != (CR)0) tb = cmac(tb, mk<CR>(w, 0), ld<CR>(A + sp));
+          }
+          acc = cmac(acc, cvt<CR>(lbnd[b]), tb);
+        }
+      } else if (l == 0) {
+        const int b = j / cr, jj = j % cr;
+        cx<CR> tb = mk<CR>(0, 0);
+        for (int sp = 0; sp < 2; ++sp) {
+          const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
+          if (w != (CR)0) tb = cmac(tb, mk<CR>(w, 0), ld<CR>(A + sp * cr + jj));
+        }
+        acc = cmul(cvt<CR>(lbnd[b]), tb);
+      } else {
+        const bool last = (l == n - 1);
+        const int b0 = last ? 0 : j / cr, b1 = last ? D : b0 + 1;
+        const int jj = last ? 0 : j % cr;
+        for (int b = b0; b < b1; ++b) {
+          for (int sp = 0; sp < 2; ++sp) {
+            const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
+            if (w == (CR)0) continue;
+            cx<CR> t = mk<CR>(0, 0);
+            for (int a = 0; a < cl; ++a)
+              t = cmac(t, cvt<CR>(B.Rp[i * xl + b * cl + a]), ld<CR>(A + (a * 2 + sp) * cr + jj));
+            acc = cmac(acc, mk<CR>(w, 0), t);
+          }
+        }
+      }
+    } else {  // ---- direct sum
+      auto pval = [&](int t) -> CR {
+        if (B.tplus[t]) return h;
+        return ((int)((B.tbits[t] >> l) & 1ull) == s) ? (CR)1 : (CR)0;
+      };
+      if (n == 1) {
+        acc = cmul(cvt<CR>(cpsi), ld<CR>(A + s));
+        for (int t = 0; t < nt; ++t) acc = cmac(acc, cvt<CR>(B.tcoef[t]), mk<CR>(pval(t), 0));
+      } else if (l == 0) {
+        if (j < cr)
+          acc = cmul(cvt<CR>(cpsi), ld<CR>(A + s * cr + j));
+        else
+          acc = cscale(cvt<CR>(B.tcoef[j - cr]), pval(j - cr));
+      } else if (l == n - 1) {
+        for (int a = 0; a < cl; ++a) acc = cmac(acc, cvt<CR>(B.Rp[i * xl + a]), ld<CR>(A + a * 2 + s));
+        for (int t = 0; t < nt; ++t) acc = cmac(acc, cvt<CR>(B.Rp[i * xl + cl + t]), mk<CR>(pval(t), 0));
+      } else {
+        if (j < cr) {
+          for (int a = 0; a < cl; ++a)
+            acc = cmac(acc, cvt<CR>(B.Rp[i * xl + a]), ld<CR>(A + (a * 2 + s) * cr + j));
+        } else {
+          acc = cscale(cvt<CR>(B.Rp[i * xl + cl + (j - cr)]), pval(j - cr));
+        }
+      }
+    }
+    B.W[e] = cvt<T>(acc);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------- sweeps
+template <class T>
+__device__ __forceinline__ void set_status(int* misc, int code) {
+  if (misc[0] == 0) misc[0] = code;
+}
+
+// One contraction followed by the QR sweep and the truncated SVD sweep.
+template <class T, class S, class CR>
+__device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* lbnd, cx<T> cpsi,
+                           int nt) {
+  const InstDesc& d = *B.d;
+  const int n = B.n;
+  // expanded bond at cut l (0 < l < n)
+  auto xb = [&](int l) -> int {
+    if (l == 0 || l == n) return 1;
+    return mode == 0 ? D * B.chi[l] : B.chi[l] + nt;
+  };
+  // ------------------------------------------------ QR sweep, left to right
+  if (threadIdx.x == 0) {
+    B.Rp[0] = mk<T>(1, 0);
+    B.qb[0] = 1;
+  }
+  __syncthreads();
+  int r = 1;
+  for (int l = 0; l < n; ++l) {
+    const int xl = xb(l), xr = xb(l + 1);
+    if (xr > d.xcap || xl > d.xcap) {
+      if (threadIdx.x == 0) set_status<T>(B.misc, kDevCapacity);
+      __syncthreads();
+      return;
+    }
+    expand_absorb<T, S, CR>(B, l, r, xl, xr, mode, op, D, lbnd, cpsi, nt);
+    const int m = 2 * r;
+    S* dst = B.slot(l);
+    if (l == n - 1) {
+      for (int e = threadIdx.x; e < m; e += blockDim.x) st(dst + e, B.W[e]);
+      if (threadIdx.x == 0) B.qb[n] = 1;
+      __syncthreads();
+      break;
+    }
+#ifdef GMPS_TRACE
+    if (threadIdx.x == 0 && blockIdx.x == 0 && l < 3) {
+      printf("qr l=%d m=%d xr=%d W:", l, m, xr);
+      for (int t = 0; t < m * xr; ++t) printf(" (%.4e,%.4e)", (double)B.W[t].re, (double)B.W[t].im);
+      printf("\n");
+    }
+    __syncthreads();
+#endif
+#ifdef GMPS_CHECK
+    __shared__ double2 chkW[64 * 32];
+    for (int e = threadIdx.x; e < m * xr && e < 64 * 32; e += blockDim.x)
+      chkW[e] = make_double2((double)B.W[e].re, (double)B.W[e].im);
+    __syncthreads();
+#endif
+    qr_householder<T>(B.W, m, xr, xr, B.tau, B.beta);
+    const int p = min(m, xr);
+    // R -> Rp (p x xr, ld xr)
+    for (int e = threadIdx.x; e < p * xr; e += blockDim.x) {
+      const int i = e / xr, c = e % xr;
+      B.Rp[e] = (c > i) ? B.W[i * xr + c] : (c == i ? B.beta[i] : mk<T>(0, 0));
+    }
+    __syncthreads();
+    qr_form_q<T>(B.W, m, p, xr, B.tau);
+#ifdef GMPS_CHECK
+    if (threadIdx.x == 0 && m * xr <= 64 * 32) {
+      double eo = 0, er = 0;
+      for (int a = 0; a < p; ++a)
+        for (int b2 = 0; b2 < p; ++b2) {
+          double re = 0, im = 0;
+          for (int i = 0; i < m; ++i) {
+            const double ar = (double)B.W[i * xr + a].re, ai = (double)B.W[i * xr + a].im;
+            const double br = (double)B.W[i * xr + b2].re, bi = (double)B.W[i * xr + b2].im;
+            re += ar * br + ai * bi;
+            im += ar * bi - ai * br;
+          }
+          eo = fmax(eo, fabs(re - (a == b2)) + fabs(im));
+        }
+      for (int i = 0; i < m; ++i)
+        for (int c2 = 0; c2 < xr; ++c2) {
+          double re = 0, im = 0;
+          for (int a = 0; a <= min(c2, p - 1); ++a) {
+            const double qr_ = (double)B.W[i * xr + a].re, qi = (double)B.W[i * xr + a].im;
+            const double rr_ = (double)B.Rp[a * xr + c2].re, ri = (double)B.Rp[a * xr + c2].im;
+            re += qr_ * rr_ - qi * ri;
+            im += qr_ * ri + qi * rr_;
+          }
+          er = fmax(er, fabs(re - chkW[i * xr + c2].x) + fabs(im - chkW[i * xr + c2].y));
+        }
+      if (eo > 1e-12 || er > 1e-12) {
+        printf("QRCHECK l=%d m=%d xr=%d orth=%.3e recon=%.3e\n", l, m, xr, eo, er);
+        for (int i = 0; i < m; ++i) {
+          for (int c2 = 0; c2 < xr; ++c2) printf(" (%.17g,%.17g)", chkW[i * xr + c2].x, chkW[i * xr + c2].y);
+          printf("\n");
+        }
+      }
+    }
+    __syncthreads();
+#endif
+    for (int e = threadIdx.x; e < m * p; e += blockDim.x) st(dst + e, B.W[(e / p) * xr + (e % p)]);
+    if (threadIdx.x == 0) B.qb[l + 1] = p;
+    __syncthreads();
+    r = p;
+  }
+  if (n == 1) {
+    // single site: renormalise only
+    S* a = B.slot(0);
+    if (threadIdx.x < 32) {
+      T s2 = 0;
+      if (threadIdx.x < 2) s2 = abs2(ld<T>(a + threadIdx.x));
+      s2 = gsum(s2, 32);
+      if (threadIdx.x == 0) {
+        if (!(s2 > 0) || !isfinite((double)s2)) set_status<T>(B.misc, kDevNumeric);
+        B.dmisc[0] += 0.5 * log((double)s2);
+        B.amps[0] = mk<T>(rsqrt(s2), 0);
+      }
+    }
+    __syncthreads();
+    const T inv = B.amps[0].re;
+    if (threadIdx.x < 2) st(a + threadIdx.x, cscale(ld<T>(a + threadIdx.x), inv));
+    __syncthreads();
+    return;
+  }
+  // ------------------------------------------------ SVD sweep, right to left
+  if (threadIdx.x == 0) B.US[0] = mk<T>(1, 0);
+  __syncthreads();
+  int kr = 1;  // bond to the right of the current site after truncation
+  const T eps_rule = B.tmisc[0];
+  const T tol_rule = B.tmisc[1];
+  for (int l = n - 1; l >= 1; --l) {
+    const int rl = B.qb[l], rr = B.qb[l + 1];
+    const S* A = B.slot(l);
+    const int c = 2 * kr;
+    // Mat = A (rl x 2 x rr) * US (rr x kr)  -> rl x (2 kr)
+    for (int e = threadIdx.x; e < rl * c; e += blockDim.x) {
+      const int i = e / c, s = (e / kr) & 1, j = e % kr;
+      cx<CR> acc = mk<CR>(0, 0);
+      for (int a = 0; a < rr; ++a) acc = cmac(acc, ld<CR>(A + (i * 2 + s) * rr + a), cvt<CR>(B.US[a * kr + j]));
+      const cx<T> v = cvt<T>(acc);
+      B.Mat[e] = v;
+      B.U[e] = v;  // copy of the input: U*S is formed from it after the rotations
+    }
+    __syncthreads();
+    // noise floor for skipping rotations: (max(m,n) eps / 4)^2 times the
+    // largest squared row norm
+    if (threadIdx.x < 32) {
+      T amax = 0;
+      for (int i = threadIdx.x; i < rl; i += 32) {
+        T s2 = 0;
+        for (int j = 0; j < c; ++j) s2 += abs2(B.Mat[i * c + j]);
+        amax = fmax(amax, s2);
+      }
+      for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, shx(amax, o));
+      if (threadIdx.x == 0) {
+        const T f = (T)max(rl, c) * eps_rule * (T)0.25f;
+        B.tmisc[8] = amax * f * f;
+      }
+    }
+    __syncthreads();
+    const int sw = jacobi_rows<T>(B.Mat, rl, c, c, d.max_sweeps, K<T>::jtolf(), B.tmisc[8]);
+    // row norms -> sigma, ranks -> perm
+    {
+      const int G = pow2_cap32(c);
+      const Grp g = make_grp(G);
+      for (int t0 = 0; t0 < rl; t0 += g.ng) {
+        const int i = t0 + g.gid;
+        T s2 = 0;
+        if (i < rl)
+          for (int j = g.lg; j < c; j += G) s2 += abs2(B.Mat[i * c + j]);
+        s2 = gsum(s2, G);
+        if (i < rl && g.lg == 0) B.sig[i] = sqrt(s2);
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rl; i += blockDim.x) {
+      const T si = B.sig[i];
+      int rank = 0;
+      for (int j = 0; j < rl; ++j) {
+        const T sj = B.sig[j];
+        rank += (sj > si) || (sj == si && j < i);
+      }
+      B.perm[rank] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (sw < 0) set_status<T>(B.misc, kDevNoConv);
+      const int swc = sw < 0 ? d.max_sweeps : sw;
+      B.misc[1] = max(B.misc[1], swc);
+      B.misc[2] += swc;
+      B.misc[3] += 1;
+      const T s0 = B.sig[B.perm[0]];
+      const T thr = fmax(tol_rule * s0, (T)max(rl, c) * eps_rule * s0);
+      int k = 0;
+      T tot = 0, kept = 0;
+      for (int t = 0; t < rl; ++t) {
+        const T st_ = B.sig[B.perm[t]];
+        tot += st_ * st_;
+        if (st_ > thr) ++k;
+      }
+      if (k < 1) k = 1;
+      if (k > d.chi_max) k = d.chi_max;
+      if (k > d.chicap) {
+        set_status<T>(B.misc, kDevCapacity);
+        k = d.chicap;
+      }
+      for (int t = 0; t < k; ++t) {
+        const T st_ = B.sig[B.perm[t]];
+        kept += st_ * st_;
+      }
+      if (tot > (T)0 && kept != tot) B.tmisc[2] += (tot - kept) / tot;
+      B.misc[4] = k;
+    }
+    __syncthreads();
+    const int k = B.misc[4];
+#ifdef GMPS_TRACE
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+      printf("svd l=%d rl=%d c=%d kr=%d sw=%d k=%d sig:", l, rl, c, kr, sw, k);
+      for (int t = 0; t < rl; ++t) printf(" %.6e", (double)B.sig[B.perm[t]]);
+      printf(" | Mat0:");
+      for (int t = 0; t < c; ++t) printf(" (%.4e,%.4e)", (double)B.Mat[t].re, (double)B.Mat[t].im);
+      printf("\n");
+    }
+    __syncthreads();
+#endif
+    // new site l = rows of V^dag (k x 2 x kr); US_l = U^dag[:, perm] * sigma (rl x k)
+    S* dst = B.slot(l);
+    for (int e = threadIdx.x; e < k * c; e += blockDim.x) {
+      const int t = e / c, j = e % c;
+      const int pr = B.perm[t];
+      const T inv = (T)1 / B.sig[pr];
+      st(dst + e, cscale(B.Mat[pr * c + j], inv));
+    }
+    // U S = Mat_in V: column t is Mat_in times conj(row perm_t) / sigma_t (the
+    // previous US was consumed when Mat was formed)
+    for (int e = threadIdx.x; e < rl * k; e += blockDim.x) {
+      const int i = e / k, t = e % k;
+      const int pr = B.perm[t];
+      cx<T> acc = mk<T>(0, 0);
+      for (int j = 0; j < c; ++j) acc = cmacc(acc, B.Mat[pr * c + j], B.U[i * c + j]);
+      B.US[e] = cscale(acc, (T)1 / B.sig[pr]);
+    }
+    if (threadIdx.x == 0) B.chi[l] = k;
+    __syncthreads();
+#ifdef GMPS_CHECK
+    if (threadIdx.x == 0) {
+      double eo = 0, er = 0;
+      for (int a = 0; a < k; ++a)
+        for (int b2 = 0; b2 < k; ++b2) {
+          double re = 0, im = 0;
+          for (int j = 0; j < c; ++j) {
+            const cx<T> x = ld<T>(dst + a * c + j), y = ld<T>(dst + b2 * c + j);
+            re += (double)x.re * (double)y.re + (double)x.im * (double)y.im;
+            im += (double)x.re * (double)y.im - (double)x.im * (double)y.re;
+          }
+          eo = fmax(eo, fabs(re - (a == b2)) + fabs(im));
+        }
+      for (int i = 0; i < rl; ++i)
+        for (int j = 0; j < c; ++j) {
+          double re = 0, im = 0;
+          for (int t = 0; t < k; ++t) {
+            const cx<T> u = B.US[i * k + t], v = ld<T>(dst + t * c + j);
+            re += (double)u.re * (double)v.re - (double)u.im * (double)v.im;
+            im += (double)u.re * (double)v.im + (double)u.im * (double)v.re;
+          }
+          er = fmax(er, fabs(re - (double)B.U[i * c + j].re) + fabs(im - (double)B.U[i * c + j].im));
+        }
+      if (eo > 1e-12 || er > 1e-12) {
+        printf("SVDCHECK l=%d rl=%d c=%d k=%d sw=%d orth=%.3e recon=%.3e sig:", l, rl, c, k, sw, eo, er);
+        for (int t = 0; t < rl; ++t) printf(" %.6e", (double)B.sig[B.perm[t]]);
+        printf("\n");
+        for (int i = 0; i < rl; ++i) {
+          for (int j = 0; j < c; ++j) printf(" (%.17g,%.17g)", (double)B.U[i * c + j].re, (double)B.U[i * c + j].im);
+          printf("\n");
+        }
+      }
+    }
+    __syncthreads();
+#endif
+    kr = k;
+  }
+  // ------------------------------------------------ site 0 and renormalisation
+  {
+    const int rr = B.qb[1];
+    S* A = B.slot(0);
+    const int c = 2 * kr;
+    for (int e = threadIdx.x; e < c; e += blockDim.x) {
+      const int s = e / kr, j = e % kr;
+      cx<CR> acc = mk<CR>(0, 0);
+      for (int a = 0; a < rr; ++a) acc = cmac(acc, ld<CR>(A + s * rr + a), cvt<CR>(B.US[a * kr + j]));
+      B.Mat[e] = cvt<T>(acc);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      T s2 = 0;
+      for (int e = threadIdx.x; e < c; e += 32) s2 += abs2(B.Mat[e]);
+      s2 = gsum(s2, 32);
+      if (threadIdx.x == 0) {
+        if (!(s2 > 0) || !isfinite((double)s2)) set_status<T>(B.misc, kDevNumeric);
+        B.dmisc[0] += 0.5 * log((double)s2);
+        B.amps[0] = mk<T>(rsqrt(s2), 0);
+        B.chi[0] = 1;
+      }
+    }
+    __syncthreads();
+    const T inv = B.amps[0].re;
+    for (int e = threadIdx.x; e < c; e += blockDim.x) st(A + e, cscale(B.Mat[e], inv));
+    __syncthreads();
+  }
+}
+
+// <target_t|psi> for product-state targets (basis strings or |+>^n), by the
+// chain v <- v A_l[:, b_l, :] (or v (A_l[:,0,:]+A_l[:,1,:])/sqrt 2); one warp
+// per target, lanes over the right bond (<= 64).
+template <class T, class S, class CR>
+__device__ void chain_targets(Blk<T, S>& B, int nt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const CR h = K<CR>::isq2();
+  for (int t = warp; t < nt; t += nw) {
+    const bool plus = B.tplus[t];
+    const unsigned long long bits = B.tbits[t];
+    cx<CR> v0 = mk<CR>(lane == 0 ? (CR)1 : (CR)0, 0), v1 = mk<CR>(0, 0);
+    for (int l = 0; l < B.n; ++l) {
+      const int cl = B.chi[l], cr = B.chi[l + 1];
+      const S* A = B.slot(l);
+      const int b = (int)((bits >> l) & 1ull);
+      cx<CR> n0 = mk<CR>(0, 0), n1 = mk<CR>(0, 0);
+      for (int i = 0; i < cl; ++i) {
+        const cx<CR> src = (i < 32) ? v0 : v1;
+        cx<CR> vi;
+        vi.re = shidx(src.re, i & 31);
+        vi.im = shidx(src.im, i & 31);
+        if (lane < cr) {
+          cx<CR> a = plus ? cscale(cadd(ld<CR>(A + (i * 2) * cr + lane), ld<CR>(A + (i * 2 + 1) * cr + lane)), h)
+                          : ld<CR>(A + (i * 2 + b) * cr + lane);
+          n0 = cmac(n0, vi, a);
+        }
+        if (lane + 32 < cr) {
+          cx<CR> a = plus ? cscale(cadd(ld<CR>(A + (i * 2) * cr + lane + 32), ld<CR>(A + (i * 2 + 1) * cr + lane + 32)), h)
+                          : ld<CR>(A + (i * 2 + b) * cr + lane + 32);
+          n1 = cmac(n1, vi, a);
+        }
+      }
+      v0 = n0;
+      v1 = n1;
+    }
+    if (lane == 0) B.amps[t] = cvt<T>(v0);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------ the kernel
+template <class T, class S, class CR>
+__global__ void __launch_bounds__(1024) iterate_kernel(const InstDesc* descs, int count, int* queue) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_idx;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = (count == 1) ? (blockIdx.x == 0 ? 0 : count) : atomicAdd(queue, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= count) break;
+    if (count == 1 && blockIdx.x != 0) break;
+    const InstDesc& d = descs[idx];
+    const int n = d.n;
+    size_t site_bytes = 0;
+    if (d.resident) site_bytes = (size_t)d.site_off[n] * sizeof(S);
+    const SmemPlan P = make_plan(n, d.M, d.xcap, d.chicap, sizeof(T), site_bytes);
+    Blk<T, S> B;
+    B.d = &d;
+    B.n = n;
+    B.off = d.site_off;
+    B.chi = (int*)(smem + P.off_chi);
+    B.qb = (int*)(smem + P.off_qb);
+    unsigned char* tb = smem + P.off_terms;
+    B.tbits = (unsigned long long*)tb;
+    B.tcoef = (cx<T>*)(tb + sizeof(unsigned long long) * (d.M + 2));
+    B.tplus = (int*)(tb + (sizeof(unsigned long long) + 2 * sizeof(T)) * (d.M + 2));
+    B.amps = (cx<T>*)(smem + P.off_amps);
+    B.misc = (int*)(smem + P.off_misc);
+    B.dmisc = (double*)(smem + P.off_misc + 128);
+    B.tmisc = (T*)(smem + P.off_misc + 256);
+    B.Rp = (cx<T>*)(smem + P.off_rprev);
+    B.W = (cx<T>*)(smem + P.off_w);
+    B.tau = (T*)(smem + P.off_tau);
+    B.beta = (cx<T>*)(smem + P.off_beta);
+    B.Mat = (cx<T>*)(smem + P.off_mat);
+    B.U = (cx<T>*)(smem + P.off_u);
+    B.US = (cx<T>*)(smem + P.off_us);
+    B.sig = (T*)(smem + P.off_sig);
+    B.perm = (int*)(smem + P.off_perm);
+    S* gsites = (S*)d.sites;
+    if (d.resident) {
+      S* ssites = (S*)(smem + P.off_sites);
+      for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) ssites[e] = gsites[e];
+      B.sites = ssites;
+    } else {
+      B.sites = gsites;
+    }
+    DevStats* ds = d.stats;
+    for (int l = threadIdx.x; l <= n; l += blockDim.x) B.chi[l] = ds->chi[l];
+    if (threadIdx.x == 0) {
+      B.misc[0] = ds->status;
+      B.misc[1] = ds->max_jacobi_sweeps;
+      B.misc[2] = 0;
+      B.misc[3] = 0;
+      B.dmisc[0] = ds->log_norm;
+      B.dmisc[1] = ds->discarded;
+      B.tmisc[0] = (T)d.trunc_eps;
+      B.tmisc[1] = (T)d.tol;
+      B.tmisc[2] = (T)0;
+    }
+    __syncthreads();
+    const int M = d.M;
+    long long done = 0;
+    for (long long it = 0; it < d.k; ++it) {
+      if (B.misc[0] != 0) break;
+      const long long pi = d.phase_offset + it;
+      // e^{i phi} - 1 and 1 - e^{i psi} in FP64 (e^{i pi} = -1 exactly for
+      // the plain-Grover default), computed once and broadcast.
+      if (threadIdx.x == 0) {
+        double cphi = -1.0, sphi = 0.0, cpsi_ = -1.0, spsi = 0.0;
+        if (d.phi) sincos(d.phi[pi], &sphi, &cphi);
+        if (d.psi) sincos(d.psi[pi], &spsi, &cpsi_);
+        B.tmisc[3] = (T)(cphi - 1.0);
+        B.tmisc[4] = (T)sphi;
+        B.tmisc[5] = (T)(1.0 - cpsi_);
+        B.tmisc[6] = (T)(-spsi);
+        B.tmisc[7] = (T)d.inv_sqrt_N;
+      }
+      __syncthreads();
+      const cx<T> em1 = mk<T>(B.tmisc[3], B.tmisc[4]);   // e^{i phi} - 1
+      const cx<T> opsi = mk<T>(B.tmisc[5], B.tmisc[6]);  // 1 - e^{i psi}
+      if (d.apply == 0) {
+        // O as an MPO of bond M+1: left boundary (1, e^{i phi}-1, ...)
+        for (int a = threadIdx.x; a <= M; a += blockDim.x) B.tcoef[a] = a == 0 ? mk<T>(1, 0) : em1;
+        __syncthreads();
+        sweep_pair<T, S, CR>(B, 0, 0, M + 1, B.tcoef, mk<T>(1, 0), 0);
+        if (B.misc[0] != 0) break;
+        // D as an MPO of bond 2: left boundary (-1, 1 - e^{i psi})
+        if (threadIdx.x == 0) {
+          B.tcoef[0] = mk<T>(-1, 0);
+          B.tcoef[1] = opsi;
+        }
+        __syncthreads();
+        sweep_pair<T, S, CR>(B, 0, 1, 2, B.tcoef, mk<T>(1, 0), 0);
+      } else if (d.apply == 1) {
+        // O|p> = |p> + (e^{i phi}-1) sum_w p(w)|w>
+        for (int t = threadIdx.x; t < M; t += blockDim.x) {
+          B.tbits[t] = d.marked[t];
+          B.tplus[t] = 0;
+        }
+        __syncthreads();
+        chain_targets<T, S, CR>(B, M);
+        for (int t = threadIdx.x; t < M; t += blockDim.x) B.tcoef[t] = cmul(em1, B.amps[t]);
+        __syncthreads();
+        sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(1, 0), M);
+        if (B.misc[0] != 0) break;
+        // D|p> = (1 - e^{i psi}) <s|p> |s> - |p>
+        if (threadIdx.x == 0) {
+          B.tbits[0] = 0;
+          B.tplus[0] = 1;
+        }
+        __syncthreads();
+        chain_targets<T, S, CR>(B, 1);
+        if (threadIdx.x == 0) B.tcoef[0] = cmul(opsi, B.amps[0]);
+        __syncthreads();
+        sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), 1);
+      } else {
+        // G|p> = -|p> - (e^{i phi}-1) sum_w p(w)|w> + (1-e^{i psi}) <s|O p> |s>
+        for (int t = threadIdx.x; t <= M; t += blockDim.x) {
+          B.tbits[t] = t < M ? d.marked[t] : 0ull;
+          B.tplus[t] = t == M;
+        }
+        __syncthreads();
+        chain_targets<T, S, CR>(B, M + 1);
+        if (threadIdx.x == 0) {
+          cx<T> sum = mk<T>(0, 0);
+          for (int t = 0; t < M; ++t) sum = cadd(sum, B.amps[t]);
+          const cx<T> so = cadd(B.amps[M], cscale(cmul(em1, sum), B.tmisc[7]));
+          B.tcoef[M] = cmul(opsi, so);
+        }
+        for (int t = threadIdx.x; t < M; t += blockDim.x) {
+          const cx<T> c = cmul(em1, B.amps[t]);
+          B.tcoef[t] = mk<T>(-c.re, -c.im);
+        }
+        __syncthreads();
+        sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), M + 1);
+      }
+      __syncthreads();
+      if (B.misc[0] == 0) ++done;
+    }
+    __syncthreads();
+    if (d.resident) {
+      const S* ssites = B.sites;
+      for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) gsites[e] = ssites[e];
+    }
+    for (int l = threadIdx.x; l <= n; l += blockDim.x) ds->chi[l] = B.chi[l];
+    if (threadIdx.x == 0) {
+      ds->iterations += done;
+      ds->status = B.misc[0];
+      ds->max_jacobi_sweeps = B.misc[1];
+      ds->jacobi_sweeps += B.misc[2];
+      ds->svd_count += B.misc[3];
+      ds->log_norm = B.dmisc[0];
+      ds->discarded = B.dmisc[1] + (double)B.tmisc[2];
+    }
+    __syncthreads();
+    if (count == 1) break;
+  }
+}
+
+// ------------------------------------------------------------------ init
+template <class S>
+__global__ void init_kernel(const InstDesc* descs, int count) {
+  const int idx = blockIdx.x;
+  if (idx >= count) return;
+  const InstDesc& d = descs[idx];
+  S* sites = (S*)d.sites;
+  const double h = 0.70710678118654752440;
+  for (int l = threadIdx.x; l < d.n; l += blockDim.x) {
+    S* a = sites + d.site_off[l];
+    st(a, mk<double>(h, 0.0));
+    st(a + 1, mk<double>(h, 0.0));
+  }
+  DevStats* ds = d.stats;
+  for (int l = threadIdx.x; l <= d.n; l += blockDim.x) ds->chi[l] = 1;
+  if (threadIdx.x == 0) {
+    ds->iterations = 0;
+    ds->jacobi_sweeps = 0;
+    ds->svd_count = 0;
+    ds->max_jacobi_sweeps = 0;
+    ds->status = 0;
+    ds->log_norm = 0.0;
+    ds->discarded = 0.0;
+  }
+}
+
+// ------------------------------------------------------------ amplitudes
+// <x|psi> = prod_l A_l[:, x_l, :]: one warp per bitstring.
+template <class S>
+__global__ void amplitude_kernel(const InstDesc* descs, int inst, const unsigned long long* bits,
+                                 int nbits, double* out) {
+  const InstDesc& d = descs[inst];
+  const S* sites = (const S*)d.sites;
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= nbits) return;
+  const unsigned long long x = bits[w];
+  const int* chi = d.stats->chi;
+  cx<double> v0 = mk<double>(lane == 0 ? 1.0 : 0.0, 0.0), v1 = mk<double>(0, 0);
+  for (int l = 0; l < d.n; ++l) {
+    const int cl = chi[l], cr = chi[l + 1];
+    const S* A = sites + d.site_off[l];
+    const int b = (int)((x >> l) & 1ull);
+    cx<double> n0 = mk<double>(0, 0), n1 = mk<double>(0, 0);
+    for (int i = 0; i < cl; ++i) {
+      const cx<double> src = (i < 32) ? v0 : v1;
+      cx<double> vi;
+      vi.re = __shfl_sync(0xffffffffu, src.re, i & 31);
+      vi.im = __shfl_sync(0xffffffffu, src.im, i & 31);
+      if (lane < cr) n0 = cmac(n0, vi, ld<double>(A + (i * 2 + b) * cr + lane));
+      if (lane + 32 < cr) n1 = cmac(n1, vi, ld<double>(A + (i * 2 + b) * cr + lane + 32));
+    }
+    v0 = n0;
+    v1 = n1;
+  }
+  if (lane == 0) {
+    out[2 * w] = v0.re;
+    out[2 * w + 1] = v0.im;
+  }
+}
+
+// P_marked of every instance of a batch: one block per instance, one warp
+// per marked string, chain products as above.
+template <class S>
+__global__ void batch_prob_kernel(const InstDesc* descs, int count, double* out) {
+  const int inst = blockIdx.x;
+  if (inst >= count) return;
+  const InstDesc& d = descs[inst];
+  const S* sites = (const S*)d.sites;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double part[32];
+  double acc = 0.0;
+  const int* chi = d.stats->chi;
+  for (int t = warp; t < d.M; t += nw) {
+    const unsigned long long x = d.marked[t];
+    cx<double> v0 = mk<double>(lane == 0 ? 1.0 : 0.0, 0.0), v1 = mk<double>(0, 0);
+    for (int l = 0; l < d.n; ++l) {
+      const int cl = chi[l], cr = chi[l + 1];
+      const S* A = sites + d.site_off[l];
+      const int b = (int)((x >> l) & 1ull);
+      cx<double> n0 = mk<double>(0, 0), n1 = mk<double>(0, 0);
+      for (int i = 0; i < cl; ++i) {
+        const cx<double> src = (i < 32) ? v0 : v1;
+        cx<double> vi;
+        vi.re = __shfl_sync(0xffffffffu, src.re, i & 31);
+        vi.im = __shfl_sync(0xffffffffu, src.im, i & 31);
+        if (lane < cr) n0 = cmac(n0, vi, ld<double>(A + (i * 2 + b) * cr + lane));
+        if (lane + 32 < cr) n1 = cmac(n1, vi, ld<double>(A + (i * 2 + b) * cr + lane + 32));
+      }
+      v0 = n0;
+      v1 = n1;
+    }
+    if (lane == 0) acc += abs2(v0);
+  }
+  if (lane == 0) part[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += part[w];
+    out[inst] = s;
+  }
+}
+
+// ------------------------------------------------------------ sampling
+// Philox4x64-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of
+// (x0,x1,x2,x3) <- (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1,
+// lo(M0 x0)) with the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    const unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    const unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// Perfect sampling on the right-canonical chain: one thread per shot, the
+// conditional probabilities p_b = |v A_l[:, b, :]|^2 in FP64.
+template <class S, int CH>
+__global__ void sample_kernel(const InstDesc* descs, int inst, long long shots, unsigned long long seed,
+                              unsigned long long* out, double* margin) {
+  const long long shot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (shot >= shots) return;
+  const InstDesc& d = descs[inst];
+  const S* sites = (const S*)d.sites;
+  const int* chi = d.stats->chi;
+  cx<double> v[CH], w0[CH], w1[CH];
+  v[0] = mk<double>(1.0, 0.0);
+  unsigned long long bits = 0;
+  double mg = 1e300;
+  for (int l = 0; l < d.n; ++l) {
+    const int cl = chi[l], cr = chi[l + 1];
+    const S* A = sites + d.site_off[l];
+    double p0 = 0.0, p1 = 0.0;
+    for (int j = 0; j < cr; ++j) {
+      cx<double> a0 = mk<double>(0, 0), a1 = mk<double>(0, 0);
+      for (int i = 0; i < cl; ++i) {
+        a0 = cmac(a0, v[i], ld<double>(A + (i * 2) * cr + j));
+        a1 = cmac(a1, v[i], ld<double>(A + (i * 2 + 1) * cr + j));
+      }
+      w0[j] = a0;
+      w1[j] = a1;
+      p0 += abs2(a0);
+      p1 += abs2(a1);
+    }
+    unsigned long long c[4] = {(unsigned long long)shot, (unsigned long long)l, 0ull, 0ull};
+    philox4x64_10(c, seed, 0ull);
+    const double u = (double)(c[0] >> 11) * 0x1.0p-53;
+    const double tot = p0 + p1;
+    const int b = (u * tot >= p0) ? 1 : 0;
+    if (margin) mg = fmin(mg, fabs(u - p0 / tot));
+    bits |= (unsigned long long)b << l;
+    const double inv = rsqrt(b ? p1 : p0);
+    for (int j = 0; j < cr; ++j) v[j] = cscale(b ? w1[j] : w0[j], inv);
+  }
+  out[shot] = bits;
+  if (margin) margin[shot] = mg;
+}
+
+// Copy the chain of one instance into another slab (checkpoints).
+template <class S>
+__global__ void copy_sites_kernel(const InstDesc* src, const InstDesc* dst) {
+  const long long total = src->site_off[src->n];
+  const S* a = (const S*)src->sites;
+  S* b = (S*)dst->sites;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    b[e] = a[e];
+  if (blockIdx.x == 0) {
+    const int* c0 = src->stats->chi;
+    int* c1 = dst->stats->chi;
+    for (int l = threadIdx.x; l <= src->n; l += blockDim.x) c1[l] = c0[l];
+    if (threadIdx.x == 0) {
+      dst->stats->status = src->stats->status;
+      dst->stats->log_norm = src->stats->log_norm;
+    }
+  }
+}
+
+// ------------------------------------------------------------ launchers
+size_t storage_bytes(int dtype) { return dtype == 1 ? sizeof(float2) : (dtype == 2 ? sizeof(dw2) : sizeof(double2)); }
+size_t linalg_real_bytes(int dtype) { return dtype == 2 ? sizeof(dw) : sizeof(double); }
+
+int max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+cudaError_t launch_init(const InstDesc* d_desc, int count, int dtype, int threads, cudaStream_t stream) {
+  (void)threads;
+  if (dtype == 1)
+    init_kernel<float2><<<count, 64, 0, stream>>>(d_desc, count);
+  else if (dtype == 2)
+    init_kernel<dw2><<<count, 64, 0, stream>>>(d_desc, count);
+  else
+    init_kernel<double2><<<count, 64, 0, stream>>>(d_desc, count);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <class T, class S, class CR>
+static cudaError_t launch_iter_t(const InstDesc* d_desc, int count, int* d_queue, int threads, size_t smem,
+                                 int grid, cudaStream_t stream) {
+  auto k = iterate_kernel<T, S, CR>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, stream>>>(d_desc, count, d_queue);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iterate(const InstDesc* d_desc, int count, int* d_queue, int dtype, int threads,
+                           size_t smem, int grid, cudaStream_t stream) {
+  if (dtype == 1) return launch_iter_t<double, float2, float>(d_desc, count, d_queue, threads, smem, grid, stream);
+  if (dtype == 2) return launch_iter_t<dw, dw2, dw>(d_desc, count, d_queue, threads, smem, grid, stream);
+  return launch_iter_t<double, double2, double>(d_desc, count, d_queue, threads, smem, grid, stream);
+}
+
+cudaError_t launch_amplitudes(const InstDesc* d_desc, int inst, int dtype, const unsigned long long* d_bits,
+                              int nbits, double* d_out, cudaStream_t stream) {
+  const int warps = 4;
+  const int grid = (nbits + warps - 1) / warps;
+  if (dtype == 1)
+    amplitude_kernel<float2><<<grid, 32 * warps, 0, stream>>>(d_desc, inst, d_bits, nbits, d_out);
+  else if (dtype == 2)
+    amplitude_kernel<dw2><<<grid, 32 * warps, 0, stream>>>(d_desc, inst, d_bits, nbits, d_out);
+  else
+    amplitude_kernel<double2><<<grid, 32 * warps, 0, stream>>>(d_desc, inst, d_bits, nbits, d_out);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_prob(const InstDesc* d_desc, int count, int dtype, double* d_p, cudaStream_t stream) {
+  if (dtype == 1)
+    batch_prob_kernel<float2><<<count, 128, 0, stream>>>(d_desc, count, d_p);
+  else if (dtype == 2)
+    batch_prob_kernel<dw2><<<count, 128, 0, stream>>>(d_desc, count, d_p);
+  else
+    batch_prob_kernel<double2><<<count, 128, 0, stream>>>(d_desc, count, d_p);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t launch_sample_s(const InstDesc* d_desc, int inst, int chmax, long long shots,
+                                   unsigned long long seed, unsigned long long* d_bits, double* d_margin,
+                                   cudaStream_t stream) {
+  const int threads = 128;
+  const long long grid = (shots + threads - 1) / threads;
+  if (chmax <= 4)
+    sample_kernel<S, 4><<<(unsigned)grid, threads, 0, stream>>>(d_desc, inst, shots, seed, d_bits, d_margin);
+  else if (chmax <= 16)
+    sample_kernel<S, 16><<<(unsigned)grid, threads, 0, stream>>>(d_desc, inst, shots, seed, d_bits, d_margin);
+  else if (chmax <= 64)
+    sample_kernel<S, 64><<<(unsigned)grid, threads, 0, stream>>>(d_desc, inst, shots, seed, d_bits, d_margin);
+  else
+    return cudaErrorInvalidValue;
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const InstDesc* d_desc, int inst, int dtype, int chmax, long long shots,
+                          unsigned long long seed, unsigned long long* d_bits, double* d_margin,
+                          cudaStream_t stream) {
+  if (dtype == 1) return launch_sample_s<float2>(d_desc, inst, chmax, shots, seed, d_bits, d_margin, stream);
+  if (dtype == 2) return launch_sample_s<dw2>(d_desc, inst, chmax, shots, seed, d_bits, d_margin, stream);
+  return launch_sample_s<double2>(d_desc, inst, chmax, shots, seed, d_bits, d_margin, stream);
+}
+
+cudaError_t launch_copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int dtype, cudaStream_t stream) {
+  if (dtype == 1)
+    copy_sites_kernel<float2><<<32, 256, 0, stream>>>(d_src, d_dst);
+  else if (dtype == 2)
+    copy_sites_kernel<dw2><<<32, 256, 0, stream>>>(d_src, d_dst);
+  else
+    copy_sites_kernel<double2><<<32, 256, 0, stream>>>(d_src, d_dst);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace gmps

@@ -1,0 +1,196 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mps as omps
+from oracle import reduced
+from oracle import statevector as sv
+from paper_2601_03832_gb300 import inputs
+from tests.gpu_util import dense_from_sites, right_orthonormal_error
+
+pytestmark = pytest.mark.gpu
+
+TOL_P_F64 = 1e-10        # FP64 marked probability (plain form)
+TOL_AMP_F64 = 1e-11      # FP64 amplitudes, small n
+# complex64 storage and contraction (FP64 QR/SVD): per-result bounds measured
+# on the small configuration and stated with margin
+TOL_P_C64 = 2e-6
+TOL_AMP_C64 = 2e-6
+TOL = {"c128": (TOL_P_F64, TOL_AMP_F64), "dw": (TOL_P_F64, TOL_AMP_F64), "c64": (TOL_P_C64, TOL_AMP_C64)}
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_03832_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.mark.parametrize("dtype", ["c128", "dw", "c64"])
+@pytest.mark.parametrize("apply", ["mpo", "split", "fused"])
+def test_small_config_closed_form(B, apply, dtype):
+    tp, ta = TOL[dtype]
+    inst = inputs.config_small()
+    g = B.GroverMPS(inst.n, inst.marked, dtype=dtype, apply=apply, chi_max=inst.chi_max)
+    g.iterate(inst.k)
+    P, aw, ar = reduced.closed_form(inst.n, 1, inst.k)
+    assert abs(g.prob_marked() - P) <= tp
+    a = g.amplitude(inst.marked[0])
+    assert abs(a.real - aw) < ta and abs(a.imag) < ta
+    st = g.stats()
+    assert st["chi"] == [1] + [2] * (inst.n - 1) + [1]
+    assert st["device_status"] == 0 and st["iterations"] == inst.k
+    sites = g.export()
+    v = dense_from_sites(sites)
+    ref = sv.grover(inst.n, inst.marked, inst.k)
+    assert np.abs(v - ref).max() < ta
+    orth = 1e-12 if dtype == "c128" else (1e-12 if dtype == "dw" else 1e-6)
+    for A in sites[1:]:
+        assert right_orthonormal_error(A) < orth
+    assert abs(np.linalg.norm(sites[0]) - 1.0) < orth
+
+
+@pytest.mark.parametrize("dtype", ["c128", "dw"])
+@pytest.mark.parametrize("apply", ["mpo", "split", "fused"])
+@pytest.mark.parametrize("n,M", [(1, 1), (2, 1), (3, 2), (5, 1), (7, 3), (9, 4), (11, 2)])
+def test_general_phases_dense(B, apply, n, M, dtype):
+    marked = inputs.marked_strings(n, M, seed=200 + 7 * n + M)
+    rng = np.random.default_rng(n * 31 + M)
+    k = 6
+    phis, psis = rng.normal(np.pi, 0.6, k), rng.normal(np.pi, 0.6, k)
+    g = B.GroverMPS(n, marked, dtype=dtype, apply=apply, chi_max=64)
+    g.iterate(k, phis, psis)
+    ref = sv.grover(n, marked, k, phis, psis)
+    v = dense_from_sites(g.export())
+    assert np.abs(v - ref).max() < TOL_AMP_F64
+    st = g.stats()
+    for cut in range(1, n):
+        assert st["chi"][cut] == reduced.exact_bond(n, marked, k, cut, phis, psis)
+
+
+def test_iterate_in_chunks_equals_one_call(B):
+    inst = inputs.config_small()
+    g1 = B.GroverMPS(inst.n, inst.marked, apply="fused", chi_max=4)
+    g1.iterate(50)
+    g2 = B.GroverMPS(inst.n, inst.marked, apply="fused", chi_max=4)
+    for _ in range(5):
+        g2.iterate(10)
+    assert abs(g1.prob_marked() - g2.prob_marked()) < 1e-13
+
+
+def test_multi_marked_split_and_fused_vs_reduced(B):
+    n, M = 24, 8
+    marked = inputs.marked_strings(n, M, seed=77)
+    k = 40
+    for apply in ("split", "fused"):
+        g = B.GroverMPS(n, marked, apply=apply, chi_max=16)
+        g.iterate(k)
+        P, aw, ar = reduced.closed_form(n, M, k)
+        assert abs(g.prob_marked() - P) < TOL_P_F64
+        for w in marked[:3]:
+            assert abs(g.amplitude(w) - aw) < 1e-11
+        st = g.stats()
+        for cut in (1, 5, 12, 23):
+            assert st["chi"][cut] == reduced.exact_bond(n, marked, k, cut)
+
+
+def test_sampling_bit_exact_small_config(B):
+    inst = inputs.config_small()
+    g = B.GroverMPS(inst.n, inst.marked, chi_max=inst.chi_max)
+    g.iterate(inst.k)
+    ref = omps.grover_iterate(omps.plus_state(inst.n), inst.marked, inst.k, inst.chi_max)
+    for shots, seed in ((4096, 2), (1, 2), (333, 12345)):
+        bits = g.sample(shots, seed)
+        obits, margin = omps.sample(ref, shots, seed)
+        ok = margin > 1e-12
+        assert ok.sum() >= shots - 2
+        assert np.array_equal(bits[ok], obits[ok])
+
+
+def test_sampling_general_state(B):
+    n, marked = 9, [3, 300, 77]
+    rng = np.random.default_rng(5)
+    phis, psis = rng.normal(np.pi, 0.5, 4), rng.normal(np.pi, 0.5, 4)
+    g = B.GroverMPS(n, marked, apply="split", chi_max=16)
+    g.iterate(4, phis, psis)
+    ref = omps.grover_iterate(omps.plus_state(n), marked, 4, 16, phis=phis, psis=psis)
+    bits = g.sample(2000, 99)
+    obits, margin = omps.sample(ref, 2000, 99)
+    ok = margin > 1e-12
+    assert np.array_equal(bits[ok], obits[ok])
+
+
+def test_truncation_chi_max_one(B):
+    """chi_max = 1 forces product-state truncation: compare with the oracle's
+    identical rule (gauge-invariant amplitudes)."""
+    n, marked = 8, [19]
+    g = B.GroverMPS(n, marked, chi_max=1)
+    g.iterate(3)
+    ref = omps.grover_iterate(omps.plus_state(n), marked, 3, 1)
+    v = dense_from_sites(g.export())
+    assert np.abs(v - omps.to_dense(ref)).max() < 1e-11
+    assert g.stats()["discarded_weight"] > 0
+
+
+def test_bad_arguments_are_rejected(B):
+    with pytest.raises(B.GMPSError) as e:
+        B.GroverMPS(5, [3, 3])
+    assert e.value.status == 1
+    with pytest.raises(B.GMPSError):
+        B.GroverMPS(5, [40])
+    with pytest.raises(B.GMPSError):
+        B.GroverMPS(0, [0])
+    with pytest.raises(B.GMPSError):
+        B.GroverMPS(4, [1], chi_max=0)
+    g = B.GroverMPS(4, [1])
+    with pytest.raises(B.GMPSError):
+        g.amplitude(1 << 5)
+    with pytest.raises(B.GMPSError):
+        g.iterate(2, np.array([0.1, np.nan]))
+
+
+def test_jacobi_sweep_limit_reports_status(B):
+    """max_sweeps = 1 cannot converge: the device reports ERR_NOCONV and the
+    handle enters its error state (no fault, no hang)."""
+    n, marked = 10, [5, 9, 100]
+    g = B.GroverMPS(n, marked, apply="split", chi_max=16, max_sweeps=1)
+    with pytest.raises(B.GMPSError) as e:
+        g.iterate(5)
+    assert e.value.status == 5
+    with pytest.raises(B.GMPSError) as e2:
+        g.iterate(1)
+    assert e2.value.status == 7
+    g.reset()
+    assert g.stats()["device_status"] == 0
+
+
+def test_caller_arena_from_torch(B):
+    import torch
+    inst = inputs.config_small()
+    nbytes = B.arena_bytes(inst.n, inst.marked, chi_max=4)
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    base = (buf.data_ptr() + 255) // 256 * 256
+    s = torch.cuda.current_stream()
+    g = B.GroverMPS(inst.n, inst.marked, chi_max=4, stream=s.cuda_stream, arena=(base, nbytes))
+    g.iterate(inst.k)
+    assert abs(g.prob_marked() - reduced.closed_form(inst.n, 1, inst.k)[0]) < TOL_P_F64
+    g.close()
+
+
+def test_batched_small(B):
+    insts = inputs.config_batched(count=12, seed=9, n_range=(6, 14), m_range=(1, 4), kcap=60, chi_max=8)
+    b = B.GroverBatch(insts, dtype="c128", apply="fused")
+    b.run(use_graph=True)
+    p, st, rc = b.result()
+    assert rc == 0 and not st.any()
+    for i, inst in enumerate(insts):
+        Pc = reduced.closed_form(inst.n, inst.M, inst.k)[0]
+        assert abs(p[i] - Pc) < TOL_P_F64
+    # replay the captured graph: same result
+    b.run(use_graph=True)
+    p2, _, _ = b.result()
+    assert np.array_equal(p, p2)
