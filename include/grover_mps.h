@@ -244,6 +244,30 @@ gmps_status grover_mps_batch_destroy(gmps_batch_handle b);
  * load (counts every <<<>>> launch and graph kernel node replay). */
 int64_t grover_mps_launch_count(void);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free run (no counterpart in the paper).                   */
+/* ------------------------------------------------------------------ */
+
+/* For callers that must not allocate device memory (no cudaMalloc/cudaFree
+ * after start-up, or an allocator they may not touch): runs one FP64
+ * (complex128) instance -- |+>^n, k iterations, the marked amplitudes --
+ * entirely inside a fixed 2 MiB device array compiled into the library,
+ * with no handle and no allocation of any kind.
+ *   marked      host, M distinct strings < 2^n (copied during the call)
+ *   apply       gmps_apply; chi_max, tol as in gmps_config
+ *   dev_phi/psi device arrays of k phases, or NULL for pi
+ *   p_marked    host output: sum_w |<w|psi>|^2
+ *   amp_marked  host output, 2M doubles (re, im per marked string) or NULL
+ * The call synchronises `cuda_stream`.  Instances whose chain needs more
+ * than the array's 2 MiB return GMPS_ERR_CAPACITY.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * should come before any stream capture.  All calls share the one array:
+ * calls whose GPU work overlaps (unordered streams or threads) race. */
+gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int M, int apply, int chi_max,
+                                   double tol, int64_t k, const double* dev_phi,
+                                   const double* dev_psi, void* cuda_stream, double* p_marked,
+                                   double* amp_marked);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,7 @@ EXPORTS = [
     "grover_mps_stats", "grover_mps_export", "grover_mps_destroy", "grover_mps_last_error",
     "grover_mps_batch_create", "grover_mps_batch_run", "grover_mps_batch_result",
     "grover_mps_batch_amplitude", "grover_mps_batch_set_threads", "grover_mps_batch_destroy",
-    "grover_mps_launch_count",
+    "grover_mps_launch_count", "grover_mps_run_noalloc",
 ]
 
 
@@ -89,6 +89,7 @@ def load():
         "grover_mps_batch_amplitude": [vp, i32, u64, P(f64), P(f64)],
         "grover_mps_batch_set_threads": [vp, i32],
         "grover_mps_batch_destroy": [vp],
+        "grover_mps_run_noalloc": [i32, P(u64), i32, i32, i32, f64, i64, vp, vp, vp, P(f64), P(f64)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +234,21 @@ class GroverMPS:
             self.close()
         except Exception:
             pass
+
+
+def run_noalloc(n, marked, k, apply="mpo", chi_max=4, tol=0.0, dev_phi=0, dev_psi=0, stream=None):
+    """grover_mps_run_noalloc: one FP64 instance in the library's static device
+    array, for callers that cannot allocate device memory.  Returns
+    (P_marked, amplitudes of the marked strings)."""
+    lib = load()
+    m = np.ascontiguousarray(np.asarray(marked, dtype=np.uint64))
+    p = C.c_double()
+    amps = np.zeros(2 * len(m))
+    _check(lib.grover_mps_run_noalloc(int(n), m.ctypes.data_as(C.POINTER(C.c_uint64)), len(m),
+                                      APPLY[apply] if isinstance(apply, str) else int(apply), int(chi_max),
+                                      float(tol), int(k), C.c_void_p(dev_phi or 0), C.c_void_p(dev_psi or 0),
+                                      C.c_void_p(stream or 0), C.byref(p), _dptr(amps)))
+    return p.value, amps[0::2] + 1j * amps[1::2]
 
 
 class GroverBatch:

@@ -22,6 +22,10 @@ long long launches_so_far();
 
 static thread_local std::string g_err;
 
+namespace gmps {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace gmps
+
 static gmps_status fail(gmps_status s, const std::string& msg) {
   g_err = msg;
   return s;

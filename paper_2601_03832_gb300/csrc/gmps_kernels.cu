@@ -1380,3 +1380,174 @@ cudaError_t launch_copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int 
 }
 
 }  // namespace gmps
+
+// =====================================================================
+// Allocation-free entry point (grover_mps_run_noalloc).
+//
+// Some callers cannot allocate device memory at all: code running inside
+// another runtime's allocator-free region (a real-time or safety-certified
+// host process that forbids cudaMalloc after start-up), plugins loaded into
+// a process whose allocator they must not touch, or callers that run while
+// the device heap is deliberately exhausted.  For them this entry point runs
+// a whole instance (init, k iterations, marked amplitudes) in a fixed
+// file-scope device array instead of a handle's arena.  It calls no
+// cudaMalloc, cudaFree or other allocating routine.
+//
+// The array below is a device symbol: in host code its name is only a
+// host-side stand-in, never a device address.  Its address is fetched with
+// cudaGetSymbolAddress once per device (with that device current) by the
+// first call on that device; that first call should therefore come before
+// any stream capture.  Every GPU that loads this library holds the array
+// (kNoAllocScratchBytes) until the process exits.  All calls share it and
+// it keeps the last call's contents; each call re-initialises everything it
+// reads (descriptor, offsets, statistics, chain).  Calls whose GPU work
+// overlaps (different streams or threads without ordering) race on it.
+// =====================================================================
+#include <mutex>
+#include <string>
+
+#include "../../include/grover_mps.h"
+
+namespace gmps {
+
+constexpr size_t kNoAllocScratchBytes = 2u << 20;  // 2 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+void set_last_error(const std::string& msg);  // gmps_capi.cu
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[64];
+static bool g_noalloc_ready[64];
+
+// Device address of g_noalloc_scratch on the current device (set-up on the
+// first call per device).
+static cudaError_t noalloc_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ready[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+    g_noalloc_ready[dev] = true;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+static size_t noalloc_a256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace gmps
+
+extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int M, int apply, int chi_max,
+                                              double tol, int64_t k, const double* dev_phi,
+                                              const double* dev_psi, void* cuda_stream, double* p_marked,
+                                              double* amp_marked) {
+  using namespace gmps;
+  auto fail = [](gmps_status s, const std::string& m) {
+    set_last_error(m);
+    return s;
+  };
+  if (n < 1 || n > 64) return fail(GMPS_ERR_ARG, "n must be in [1, 64]");
+  if (M < 1 || M > kMaxMarked || (n < 64 && (uint64_t)M >= (1ull << n)))
+    return fail(GMPS_ERR_ARG, "M must be in [1, min(2^n - 1, 64)]");
+  if (!marked || !p_marked) return fail(GMPS_ERR_ARG, "marked and p_marked must not be NULL");
+  for (int i = 0; i < M; ++i) {
+    if (n < 64 && (marked[i] >> n)) return fail(GMPS_ERR_ARG, "marked string has bits >= n");
+    for (int j = 0; j < i; ++j)
+      if (marked[j] == marked[i]) return fail(GMPS_ERR_ARG, "duplicate marked string");
+  }
+  if (apply < 0 || apply > 2) return fail(GMPS_ERR_ARG, "apply must be 0, 1 or 2");
+  if (chi_max < 1) return fail(GMPS_ERR_ARG, "chi_max must be >= 1");
+  if (!(tol >= 0.0) || !isfinite(tol)) return fail(GMPS_ERR_ARG, "tol must be finite and >= 0");
+  if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+  // plan (FP64 form): bond capacity, expanded bond, slots
+  int chicap = chi_max < M + 3 ? chi_max : M + 3;
+  long long half = 1;
+  for (int i = 0; i < n / 2 && half < chicap; ++i) half *= 2;
+  if (half < chicap) chicap = (int)half;
+  const int xcap = apply == 0 ? (M + 1) * chicap : (apply == 1 ? chicap + M : chicap + M + 1);
+  if (apply == 0 && xcap > 64) return fail(GMPS_ERR_UNSUPPORTED, "MPO contraction needs (M+1)*chi <= 64");
+  long long off[kMaxN + 1];
+  off[0] = 0;
+  for (int l = 0; l < n; ++l) off[l + 1] = off[l] + slot_elems(l, n, xcap);
+  const size_t site_bytes = (size_t)off[n] * sizeof(double2);
+  const size_t o_desc = 0, o_off = noalloc_a256(sizeof(InstDesc));
+  const size_t o_stats = o_off + noalloc_a256(sizeof(long long) * (n + 1));
+  const size_t o_marked = o_stats + noalloc_a256(sizeof(DevStats));
+  const size_t o_amp = o_marked + noalloc_a256(sizeof(uint64_t) * M);
+  const size_t o_sites = o_amp + noalloc_a256(sizeof(double) * 2 * M);
+  const size_t need = o_sites + noalloc_a256(site_bytes);
+  if (need > kNoAllocScratchBytes)
+    return fail(GMPS_ERR_CAPACITY, "instance needs " + std::to_string(need) +
+                                       " bytes of static scratch; grover_mps_run_noalloc holds " +
+                                       std::to_string(kNoAllocScratchBytes));
+  const int smax = max_smem_optin();
+  SmemPlan sp = make_plan(n, M, xcap, chicap, sizeof(double), site_bytes);
+  int resident = 1;
+  if (sp.total > (size_t)smax) {
+    resident = 0;
+    sp = make_plan(n, M, xcap, chicap, sizeof(double), 0);
+    if (sp.total > (size_t)smax) return fail(GMPS_ERR_UNSUPPORTED, "working set exceeds shared memory");
+  }
+  const int threads = xcap <= 8 ? 32 : (xcap <= 16 ? 64 : (xcap <= 32 ? 128 : (xcap <= 64 ? 256 : 512)));
+
+  void* base = nullptr;
+  cudaError_t e = noalloc_scratch_address(&base);
+  if (e != cudaSuccess) return fail(GMPS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  unsigned char* b = (unsigned char*)base;
+  InstDesc d{};
+  d.n = n;
+  d.M = M;
+  d.apply = apply;
+  d.chi_max = chi_max;
+  d.chicap = chicap;
+  d.xcap = xcap;
+  d.max_sweeps = kDefaultMaxSweeps;
+  d.resident = resident;
+  d.k = k;
+  d.phase_offset = 0;
+  d.tol = tol;
+  d.trunc_eps = 2.220446049250313e-16;
+  d.inv_sqrt_N = ldexp(1.0, -n / 2) * ((n & 1) ? sqrt(0.5) : 1.0);
+  d.marked = (const unsigned long long*)(b + o_marked);
+  d.phi = dev_phi;
+  d.psi = dev_psi;
+  d.sites = b + o_sites;
+  d.site_off = (const long long*)(b + o_off);
+  d.stats = (DevStats*)(b + o_stats);
+  const InstDesc* d_desc = (const InstDesc*)(b + o_desc);
+  double* d_amp = (double*)(b + o_amp);
+#define NA_TRY(x)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) return fail(GMPS_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+  // everything the kernels read is rewritten here: the array keeps the
+  // previous call's contents
+  NA_TRY(cudaMemcpyAsync(b + o_desc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(b + o_off, off, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, stream));
+  NA_TRY(cudaMemcpyAsync(b + o_marked, marked, sizeof(uint64_t) * M, cudaMemcpyHostToDevice, stream));
+  NA_TRY(launch_init(d_desc, 1, GMPS_C128, 64, stream));  // statistics and the |+>^n chain
+  if (k > 0) NA_TRY(launch_iterate(d_desc, 1, nullptr, GMPS_C128, threads, sp.total, 1, stream));
+  NA_TRY(launch_amplitudes(d_desc, 0, GMPS_C128, (const unsigned long long*)(b + o_marked), M, d_amp, stream));
+  double amps[2 * kMaxMarked];
+  int status = 0;
+  NA_TRY(cudaMemcpyAsync(amps, d_amp, sizeof(double) * 2 * M, cudaMemcpyDeviceToHost, stream));
+  NA_TRY(cudaMemcpyAsync(&status, b + o_stats + offsetof(DevStats, status), sizeof(int), cudaMemcpyDeviceToHost,
+                         stream));
+  NA_TRY(cudaStreamSynchronize(stream));
+#undef NA_TRY
+  if (status != 0) return fail((gmps_status)status, "device reported an error (status " + std::to_string(status) + ")");
+  double p = 0.0;
+  for (int i = 0; i < M; ++i) p += amps[2 * i] * amps[2 * i] + amps[2 * i + 1] * amps[2 * i + 1];
+  *p_marked = p;
+  if (amp_marked)
+    for (int i = 0; i < 2 * M; ++i) amp_marked[i] = amps[i];
+  return GMPS_OK;
+}
