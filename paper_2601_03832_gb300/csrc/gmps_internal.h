@@ -58,7 +58,7 @@ struct InstDesc {
 
 // Shared-memory plan of one block (bytes), identical on host and device.
 struct SmemPlan {
-  size_t off_chi, off_qb, off_terms, off_amps, off_misc;
+  size_t off_chi, off_qb, off_terms, off_amps, off_misc, off_qperm, off_qcn;
   size_t off_rprev, off_w, off_tau, off_beta;      // QR sweep
   size_t off_mat, off_u, off_us, off_sig, off_perm;  // SVD sweep (aliases QR)
   size_t off_sites;
@@ -78,6 +78,8 @@ GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, size_t rb,
   p.off_terms = o; o = align_up(o + (sizeof(unsigned long long) + sizeof(int) + cb + 8) * (M + 2), 16);
   p.off_amps = o;  o = align_up(o + cb * (M + 2), 16);
   p.off_misc = o;  o = align_up(o + 512, 16);
+  p.off_qperm = o; o = align_up(o + sizeof(int) * (size_t)xcap, 16);   // QR pivots
+  p.off_qcn = o;   o = align_up(o + rb * (size_t)xcap, 16);            // QR column norms
   size_t base = o;
   // QR-sweep working set
   size_t q = base;
@@ -88,7 +90,7 @@ GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, size_t rb,
   // SVD-sweep working set (aliases the QR one)
   size_t s = base;
   p.off_mat = s;   s = align_up(s + cb * (size_t)xcap * (2 * chicap), 16);
-  p.off_u = s;     s = align_up(s + cb * (size_t)xcap * (2 * chicap), 16);  // copy of the SVD input
+  p.off_u = s;     s = align_up(s + cb * (size_t)xcap * xcap, 16);          // accumulated rotations
   p.off_us = s;    s = align_up(s + cb * (size_t)xcap * chicap, 16);
   p.off_sig = s;   s = align_up(s + rb * (size_t)xcap, 16);
   p.off_perm = s;  s = align_up(s + sizeof(int) * (size_t)xcap, 16);

@@ -18,7 +18,10 @@ TOL_AMP_F64 = 1e-11      # FP64 amplitudes, small n
 # on the small configuration and stated with margin
 TOL_P_C64 = 2e-6
 TOL_AMP_C64 = 2e-6
-TOL = {"c128": (TOL_P_F64, TOL_AMP_F64), "dw": (TOL_P_F64, TOL_AMP_F64), "c64": (TOL_P_C64, TOL_AMP_C64)}
+# double-word FP32 (~48-bit significand): worst measured amplitude error 3e-11
+# over the general-phase cases below; stated bound 1e-10
+TOL_AMP_DW = 1e-10
+TOL = {"c128": (TOL_P_F64, TOL_AMP_F64), "dw": (TOL_P_F64, TOL_AMP_DW), "c64": (TOL_P_C64, TOL_AMP_C64)}
 
 
 @pytest.fixture(scope="module")
@@ -66,7 +69,7 @@ def test_general_phases_dense(B, apply, n, M, dtype):
     g.iterate(k, phis, psis)
     ref = sv.grover(n, marked, k, phis, psis)
     v = dense_from_sites(g.export())
-    assert np.abs(v - ref).max() < TOL_AMP_F64
+    assert np.abs(v - ref).max() < TOL[dtype][1]
     st = g.stats()
     for cut in range(1, n):
         assert st["chi"][cut] == reduced.exact_bond(n, marked, k, cut, phis, psis)
