@@ -161,8 +161,14 @@ struct gmps_ctx {
   long long iterations = 0;
   // differentiable form
   std::vector<double> phi_hist, psi_hist;
-  std::vector<Slab> ckpt;          // checkpoint c holds the state after c*every iterations
-  std::vector<Slab> work;          // per-iteration states inside a segment + costates
+  std::vector<Slab> ckpt;          // ckpt[j] holds the state after j*every iterations
+  Slab work;                       // segment recompute
+  Slab costate;                    // adjoint chain
+  int every = 8;
+  int max_iters = 0;
+  double* d_rec = nullptr;         // every * (M+1) complex
+  double* d_grad = nullptr;        // 2 * max_iters
+  double* d_ph_all = nullptr;      // 2 * max_iters
   char* diff_mem = nullptr;
   bool all_phases_explicit = true;
 };
@@ -300,6 +306,40 @@ gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps
     grover_mps_destroy(h);
     return s;
   }
+  if (cfg->differentiable) {
+    h->every = cfg->checkpoint_every > 0 ? cfg->checkpoint_every : 8;
+    h->max_iters = cfg->max_iters;
+    if (h->max_iters < 1) {
+      grover_mps_destroy(h);
+      return fail(GMPS_ERR_ARG, "differentiable handles need max_iters >= 1");
+    }
+    const int nck = h->max_iters / h->every + 1;
+    const size_t sb = slab_bytes(&h->cfg, h->plan);
+    const size_t bytes = sb * (nck + 2) + a256(sizeof(double) * 2 * (cfg->M + 1) * h->every) +
+                         2 * a256(sizeof(double) * 2 * h->max_iters);
+    cudaError_t e2 = cudaMalloc(&h->diff_mem, bytes);
+    if (e2 != cudaSuccess) {
+      grover_mps_destroy(h);
+      return fail(GMPS_ERR_OOM, "checkpoint storage");
+    }
+    char* q = h->diff_mem;
+    h->ckpt.resize(nck);
+    for (int j = 0; j < nck; ++j) q = carve_slab(q, &h->cfg, h->plan, &h->ckpt[j]);
+    q = carve_slab(q, &h->cfg, h->plan, &h->work);
+    q = carve_slab(q, &h->cfg, h->plan, &h->costate);
+    h->d_rec = (double*)q;
+    q += a256(sizeof(double) * 2 * (cfg->M + 1) * h->every);
+    h->d_grad = (double*)q;
+    q += a256(sizeof(double) * 2 * h->max_iters);
+    h->d_ph_all = (double*)q;
+    for (int j = 0; j < nck && !s; ++j) s = upload_slab(h, h->ckpt[j]);
+    if (!s) s = upload_slab(h, h->work);
+    if (!s) s = upload_slab(h, h->costate);
+    if (s) {
+      grover_mps_destroy(h);
+      return s;
+    }
+  }
   e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     grover_mps_destroy(h);
@@ -346,12 +386,13 @@ static gmps_status ensure_phase(gmps_ctx* h, size_t need) {
 }
 
 static gmps_status enqueue_iterate(gmps_ctx* h, int64_t k, const double* dphi, const double* dpsi,
-                                   const Slab& slab) {
+                                   const Slab& slab, double* rec = nullptr) {
   InstDesc d = base_desc(h, slab);
   d.k = k;
   d.phase_offset = 0;
   d.phi = dphi;
   d.psi = dpsi;
+  d.rec = rec;
   CUDA_TRY(cudaMemcpyAsync(slab.d_desc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(launch_iterate(slab.d_desc, 1, nullptr, h->cfg.dtype, h->plan.threads, h->plan.smem, 1, h->stream));
   return GMPS_OK;
@@ -362,6 +403,8 @@ gmps_status grover_mps_iterate_device(gmps_handle h, int64_t k, const double* de
   if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
   if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
   if (k == 0) return GMPS_OK;
+  if (h->cfg.differentiable)
+    return fail(GMPS_ERR_UNSUPPORTED, "differentiable handles take host phases (grover_mps_iterate)");
   gmps_status s = enqueue_iterate(h, k, dev_phi, dev_psi, h->main);
   if (s) return s;
   h->iterations += k;
@@ -393,7 +436,22 @@ gmps_status grover_mps_iterate(gmps_handle h, int64_t k, const double* host_phi,
       dpsi = h->d_phase + h->phase_cap;
     }
   }
-  if ((s = enqueue_iterate(h, k, dphi, dpsi, h->main))) return s;
+  if (h->cfg.differentiable) {
+    if (h->iterations + k > h->max_iters) return fail(GMPS_ERR_ARG, "iterations would exceed max_iters");
+    int64_t done = 0;
+    while (done < k) {
+      const int64_t pos = h->iterations + done;
+      const int64_t chunk = std::min<int64_t>(k - done, h->every - pos % h->every);
+      if ((s = enqueue_iterate(h, chunk, dphi ? dphi + done : nullptr, dpsi ? dpsi + done : nullptr, h->main)))
+        return s;
+      done += chunk;
+      if ((pos + chunk) % h->every == 0)
+        CUDA_TRY(launch_copy_sites(h->main.d_desc, h->ckpt[(pos + chunk) / h->every].d_desc, h->cfg.dtype,
+                                   h->stream));
+    }
+  } else if ((s = enqueue_iterate(h, k, dphi, dpsi, h->main))) {
+    return s;
+  }
   h->iterations += k;
   for (int64_t i = 0; i < k; ++i) {
     h->phi_hist.push_back(host_phi ? host_phi[i] : M_PI);
@@ -529,12 +587,44 @@ gmps_status grover_mps_export(gmps_handle h, double* host_out, size_t capacity, 
   return GMPS_OK;
 }
 
+static gmps_status check_slab(gmps_ctx* h, const Slab& sl, const char* what) {
+  int st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, (char*)sl.d_stats + offsetof(DevStats, status), sizeof(int),
+                           cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (st) return fail((gmps_status)st, std::string(what) + ": device reported an error");
+  return GMPS_OK;
+}
+
 gmps_status grover_mps_backward(gmps_handle h, double dL_dP, double* grad_phi, double* grad_psi) {
-  (void)dL_dP;
-  (void)grad_phi;
-  (void)grad_psi;
   if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
-  return fail(GMPS_ERR_UNSUPPORTED, "backward not built yet");
+  if (!h->cfg.differentiable) return fail(GMPS_ERR_STATE, "handle was not created differentiable");
+  if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
+  const int64_t K = h->iterations;
+  if (K == 0) return GMPS_OK;
+  if (!grad_phi || !grad_psi) return fail(GMPS_ERR_ARG, "gradient outputs are NULL");
+  const int mi = h->max_iters;
+  CUDA_TRY(cudaMemcpyAsync(h->d_ph_all, h->phi_hist.data(), sizeof(double) * K, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->d_ph_all + mi, h->psi_hist.data(), sizeof(double) * K, cudaMemcpyHostToDevice,
+                           h->stream));
+  // mu_K = Pi_W psi_K on the costate chain
+  CUDA_TRY(launch_copy_sites(h->main.d_desc, h->costate.d_desc, h->cfg.dtype, h->stream));
+  CUDA_TRY(launch_adjoint(h->costate.d_desc, h->cfg.dtype, h->plan.threads, h->plan.smem, nullptr, K, K,
+                          h->d_ph_all, h->d_ph_all + mi, dL_dP, h->d_grad, h->d_grad + mi, 1, h->stream));
+  for (int64_t j = (K - 1) / h->every; j >= 0; --j) {
+    const int64_t k_lo = j * h->every, k_hi = std::min<int64_t>(K, k_lo + h->every);
+    // recompute the segment from its checkpoint, recording <w|psi> and <s|psi>
+    CUDA_TRY(launch_copy_sites(h->ckpt[j].d_desc, h->work.d_desc, h->cfg.dtype, h->stream));
+    gmps_status s = enqueue_iterate(h, k_hi - k_lo, h->d_ph_all + k_lo, h->d_ph_all + mi + k_lo, h->work, h->d_rec);
+    if (s) return s;
+    CUDA_TRY(launch_adjoint(h->costate.d_desc, h->cfg.dtype, h->plan.threads, h->plan.smem, h->d_rec, k_lo, k_hi,
+                            h->d_ph_all, h->d_ph_all + mi, dL_dP, h->d_grad, h->d_grad + mi, 0, h->stream));
+  }
+  CUDA_TRY(cudaMemcpyAsync(grad_phi, h->d_grad, sizeof(double) * K, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(grad_psi, h->d_grad + mi, sizeof(double) * K, cudaMemcpyDeviceToHost, h->stream));
+  gmps_status s = check_slab(h, h->work, "segment recompute");
+  if (!s) s = check_slab(h, h->costate, "adjoint");
+  return s;
 }
 
 gmps_status grover_mps_destroy(gmps_handle h) {

@@ -54,6 +54,8 @@ struct InstDesc {
   void* sites;              // device slab
   const long long* site_off;  // n+1 offsets (elements of the storage type)
   DevStats* stats;          // device
+  double* rec;              // optional: before each iteration, the marked amplitudes and
+                            // <s|psi> of the chain, (M+1) complex per iteration
 };
 
 // Shared-memory plan of one block (bytes), identical on host and device.
@@ -128,6 +130,9 @@ cudaError_t launch_sample(const InstDesc* d_desc, int inst, int dtype, int chmax
                           double* d_margin, cudaStream_t stream);
 cudaError_t launch_copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int dtype,
                               cudaStream_t stream);
+cudaError_t launch_adjoint(const InstDesc* d_mu, int dtype, int threads, size_t smem, const double* rec,
+                           long long k_lo, long long k_hi, const double* phi, const double* psi, double scale,
+                           double* gphi, double* gpsi, int project, cudaStream_t stream);
 cudaError_t launch_batch_prob(const InstDesc* d_desc, int count, int dtype, double* d_p,
                               cudaStream_t stream);
 size_t storage_bytes(int dtype);      // bytes of one complex site element

@@ -1209,6 +1209,20 @@ __global__ void __launch_bounds__(1024) iterate_kernel(const InstDesc* descs, in
     for (long long it = 0; it < d.k; ++it) {
       if (B.misc[0] != 0) break;
       const long long pi = d.phase_offset + it;
+      if (d.rec) {
+        // record <w|psi> for every marked w and <s|psi> (adjoint recompute)
+        for (int t = threadIdx.x; t <= M; t += blockDim.x) {
+          B.tbits[t] = t < M ? d.marked[t] : 0ull;
+          B.tplus[t] = t == M;
+        }
+        __syncthreads();
+        chain_targets<T, S, CR>(B, M + 1);
+        for (int t = threadIdx.x; t <= M; t += blockDim.x) {
+          d.rec[(it * (M + 1) + t) * 2] = (double)B.amps[t].re;
+          d.rec[(it * (M + 1) + t) * 2 + 1] = (double)B.amps[t].im;
+        }
+        __syncthreads();
+      }
       // e^{i phi} - 1 and 1 - e^{i psi} in FP64 (e^{i pi} = -1 exactly for
       // the plain-Grover default), computed once and broadcast.
       if (threadIdx.x == 0) {
@@ -1304,6 +1318,168 @@ __global__ void __launch_bounds__(1024) iterate_kernel(const InstDesc* descs, in
     }
     __syncthreads();
     if (count == 1) break;
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+// Reverse sweep of the phase gradient of P = sum_w |<w|psi_K>|^2 over
+// iterations k_hi..k_lo+1 (1-based), on the costate chain of `descs[0]`:
+//   mu_K = Pi_W psi_K  (project != 0: built from the chain itself),
+//   nu_k = D(psi_k)^dag mu_k = D(-psi_k) mu_k,   mu_{k-1} = O(-phi_k) nu_k,
+//   dP/dphi_k = 2 Re[ i e^{i phi_k} sum_w conj(nu_k(w)) psi_{k-1}(w) ],
+//   dP/dpsi_k = 2 Re[ -i e^{i psi_k} conj(<s|mu_k>) <s|O_k psi_{k-1}> ],
+//   <s|O_k psi> = <s|psi> + (e^{i phi_k} - 1) 2^{-n/2} sum_w psi(w).
+// Each costate step is a direct-sum contraction followed by the QR and SVD
+// sweeps; the costate's norm is carried by the chain's log-norm.  rec holds
+// the forward chain's marked amplitudes and <s|psi_{k-1}> for k-1 = k_lo..k_hi-1.
+// The gradients are written scaled by `scale` (dL/dP).
+template <class T, class S, class CR>
+__global__ void __launch_bounds__(1024) adjoint_kernel(const InstDesc* descs, const double* rec, long long k_lo,
+                                                       long long k_hi, const double* phi, const double* psi,
+                                                       double scale, double* gphi, double* gpsi, int project) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const InstDesc& d = descs[0];
+  const int n = d.n, M = d.M;
+  size_t site_bytes = d.resident ? (size_t)d.site_off[n] * sizeof(S) : 0;
+  const SmemPlan P = make_plan(n, M, d.xcap, d.chicap, sizeof(T), site_bytes);
+  Blk<T, S> B;
+  B.d = &d;
+  B.n = n;
+  B.off = d.site_off;
+  B.chi = (int*)(smem + P.off_chi);
+  B.qb = (int*)(smem + P.off_qb);
+  unsigned char* tb = smem + P.off_terms;
+  B.tbits = (unsigned long long*)tb;
+  B.tcoef = (cx<T>*)(tb + sizeof(unsigned long long) * (M + 2));
+  B.tplus = (int*)(tb + (sizeof(unsigned long long) + 2 * sizeof(T)) * (M + 2));
+  B.amps = (cx<T>*)(smem + P.off_amps);
+  B.misc = (int*)(smem + P.off_misc);
+  B.dmisc = (double*)(smem + P.off_misc + 128);
+  B.tmisc = (T*)(smem + P.off_misc + 256);
+  B.qperm = (int*)(smem + P.off_qperm);
+  B.qcn = (T*)(smem + P.off_qcn);
+  B.Rp = (cx<T>*)(smem + P.off_rprev);
+  B.W = (cx<T>*)(smem + P.off_w);
+  B.tau = (T*)(smem + P.off_tau);
+  B.beta = (cx<T>*)(smem + P.off_beta);
+  B.Mat = (cx<T>*)(smem + P.off_mat);
+  B.U = (cx<T>*)(smem + P.off_u);
+  B.US = (cx<T>*)(smem + P.off_us);
+  B.sig = (T*)(smem + P.off_sig);
+  B.perm = (int*)(smem + P.off_perm);
+  S* gsites = (S*)d.sites;
+  if (d.resident) {
+    S* ssites = (S*)(smem + P.off_sites);
+    for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) ssites[e] = gsites[e];
+    B.sites = ssites;
+  } else {
+    B.sites = gsites;
+  }
+  DevStats* ds = d.stats;
+  for (int l = threadIdx.x; l <= n; l += blockDim.x) B.chi[l] = ds->chi[l];
+  __shared__ double s_g[4];
+  if (threadIdx.x == 0) {
+    B.misc[0] = ds->status;
+    B.misc[1] = ds->max_jacobi_sweeps;
+    B.misc[2] = 0;
+    B.misc[3] = 0;
+    B.dmisc[0] = project ? 0.0 : ds->log_norm;
+    B.dmisc[1] = ds->discarded;
+    B.tmisc[0] = (T)d.trunc_eps;
+    B.tmisc[1] = (T)d.tol;
+    B.tmisc[2] = (T)0;
+  }
+  __syncthreads();
+  if (project) {
+    // mu_K = sum_w psi_K(w) |w>: a direct sum without the chain's own block
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+      B.tbits[t] = d.marked[t];
+      B.tplus[t] = 0;
+    }
+    __syncthreads();
+    chain_targets<T, S, CR>(B, M);
+    for (int t = threadIdx.x; t < M; t += blockDim.x) B.tcoef[t] = B.amps[t];
+    __syncthreads();
+    sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(0, 0), M);
+  }
+  for (long long k = k_hi; k > k_lo && B.misc[0] == 0; --k) {
+    if (threadIdx.x == 0) {
+      double sp, cp, ss, cs;
+      sincos(phi[k - 1], &sp, &cp);
+      sincos(psi[k - 1], &ss, &cs);
+      B.dmisc[2] = cp;
+      B.dmisc[3] = sp;
+      B.dmisc[4] = cs;
+      B.dmisc[5] = ss;
+      B.tbits[0] = 0ull;
+      B.tplus[0] = 1;
+    }
+    __syncthreads();
+    const double cp = B.dmisc[2], sp = B.dmisc[3], cs = B.dmisc[4], ss = B.dmisc[5];
+    // <s|mu_k> of the normalised chain, scale lambda_mu = e^{log norm}
+    chain_targets<T, S, CR>(B, 1);
+    if (threadIdx.x == 0) {
+      const double lam = exp(B.dmisc[0]);
+      s_g[0] = lam * (double)B.amps[0].re;
+      s_g[1] = lam * (double)B.amps[0].im;
+      // nu = D(-psi) mu = (1 - e^{-i psi}) <s|mu> |s> - mu
+      const cx<T> c1 = mk<T>((T)(1.0 - cs), (T)ss);
+      B.tcoef[0] = cmul(c1, B.amps[0]);
+    }
+    __syncthreads();
+    sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), 1);
+    if (B.misc[0] != 0) break;
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+      B.tbits[t] = d.marked[t];
+      B.tplus[t] = 0;
+    }
+    __syncthreads();
+    chain_targets<T, S, CR>(B, M);
+    if (threadIdx.x == 0) {
+      const double lam = exp(B.dmisc[0]);
+      const double* S_ = rec + (k - 1 - k_lo) * (M + 1) * 2;
+      double zr = 0, zi = 0, sr = 0, si = 0;  // sum conj(nu) psi, sum psi
+      for (int t = 0; t < M; ++t) {
+        const double nr = (double)B.amps[t].re, ni = (double)B.amps[t].im;
+        const double pr = S_[2 * t], pim = S_[2 * t + 1];
+        zr += nr * pr + ni * pim;
+        zi += nr * pim - ni * pr;
+        sr += pr;
+        si += pim;
+      }
+      zr *= lam;
+      zi *= lam;
+      // dP/dphi = 2 Re[i e^{i phi} z] = -2 (sin(phi) zr + cos(phi) zi)
+      gphi[k - 1] = scale * (-2.0 * (sp * zr + cp * zi));
+      // <s|O psi> = <s|psi> + (e^{i phi} - 1) 2^{-n/2} sum_w psi(w)
+      const double h = d.inv_sqrt_N;
+      const double er = cp - 1.0, ei = sp;
+      const double sor = S_[2 * M] + h * (er * sr - ei * si);
+      const double soi = S_[2 * M + 1] + h * (er * si + ei * sr);
+      // q = conj(<s|mu>) <s|O psi>
+      const double qr = s_g[0] * sor + s_g[1] * soi, qi = s_g[0] * soi - s_g[1] * sor;
+      // dP/dpsi = 2 Re[-i e^{i psi} q] = 2 (sin(psi) qr + cos(psi) qi)
+      gpsi[k - 1] = scale * (2.0 * (ss * qr + cs * qi));
+      // mu_{k-1} = O(-phi) nu = nu + (e^{-i phi} - 1) sum_w nu(w)|w>
+      const cx<T> c2 = mk<T>((T)(cp - 1.0), (T)(-sp));
+      for (int t = 0; t < M; ++t) B.tcoef[t] = cmul(c2, B.amps[t]);
+    }
+    __syncthreads();
+    sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(1, 0), M);
+  }
+  __syncthreads();
+  if (d.resident) {
+    const S* ssites = B.sites;
+    for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) gsites[e] = ssites[e];
+  }
+  for (int l = threadIdx.x; l <= n; l += blockDim.x) ds->chi[l] = B.chi[l];
+  if (threadIdx.x == 0) {
+    ds->status = B.misc[0];
+    ds->max_jacobi_sweeps = B.misc[1];
+    ds->jacobi_sweeps += B.misc[2];
+    ds->svd_count += B.misc[3];
+    ds->log_norm = B.dmisc[0];
+    ds->discarded = B.dmisc[1] + (double)B.tmisc[2];
   }
 }
 
@@ -1536,6 +1712,31 @@ cudaError_t launch_iterate(const InstDesc* d_desc, int count, int* d_queue, int 
   if (dtype == 1) return launch_iter_t<double, float2, float>(d_desc, count, d_queue, threads, smem, grid, stream);
   if (dtype == 2) return launch_iter_t<dw, dw2, dw>(d_desc, count, d_queue, threads, smem, grid, stream);
   return launch_iter_t<double, double2, double>(d_desc, count, d_queue, threads, smem, grid, stream);
+}
+
+template <class T, class S, class CR>
+static cudaError_t launch_adj_t(const InstDesc* d_mu, int threads, size_t smem, const double* rec, long long k_lo,
+                                long long k_hi, const double* phi, const double* psi, double scale, double* gphi,
+                                double* gpsi, int project, cudaStream_t stream) {
+  auto k = adjoint_kernel<T, S, CR>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<1, threads, smem, stream>>>(d_mu, rec, k_lo, k_hi, phi, psi, scale, gphi, gpsi, project);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const InstDesc* d_mu, int dtype, int threads, size_t smem, const double* rec,
+                           long long k_lo, long long k_hi, const double* phi, const double* psi, double scale,
+                           double* gphi, double* gpsi, int project, cudaStream_t stream) {
+  if (dtype == 1)
+    return launch_adj_t<double, float2, float>(d_mu, threads, smem, rec, k_lo, k_hi, phi, psi, scale, gphi, gpsi,
+                                               project, stream);
+  if (dtype == 2)
+    return launch_adj_t<dw, dw2, dw>(d_mu, threads, smem, rec, k_lo, k_hi, phi, psi, scale, gphi, gpsi, project,
+                                     stream);
+  return launch_adj_t<double, double2, double>(d_mu, threads, smem, rec, k_lo, k_hi, phi, psi, scale, gphi, gpsi,
+                                               project, stream);
 }
 
 cudaError_t launch_amplitudes(const InstDesc* d_desc, int inst, int dtype, const unsigned long long* d_bits,
