@@ -42,10 +42,12 @@ static gmps_status cuda_fail(cudaError_t e, const char* where) {
 static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
 // eps of the rank rule sigma_i > max(tol, max(m,n) eps) sigma_0: the unit of
-// the storage precision (FP32 for complex64, 2^-46 for double-word, FP64).
+// the storage precision (FP32 for complex64, FP64), and for double-word the
+// accumulated rounding of a QR + Jacobi chain, 2^-42, so that rounding noise
+// is never kept as a Schmidt direction.
 static double trunc_eps_for(int dtype) {
   if (dtype == GMPS_C64_F64SVD) return 1.1920928955078125e-07;
-  if (dtype == GMPS_DW) return 1.4210854715202004e-14;
+  if (dtype == GMPS_DW) return 2.2737367544323206e-13;
   return 2.220446049250313e-16;
 }
 

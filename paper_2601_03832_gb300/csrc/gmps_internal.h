@@ -60,7 +60,7 @@ struct InstDesc {
 
 // Shared-memory plan of one block (bytes), identical on host and device.
 struct SmemPlan {
-  size_t off_chi, off_qb, off_terms, off_amps, off_misc, off_qperm, off_qcn;
+  size_t off_chi, off_qb, off_soff, off_terms, off_amps, off_misc, off_qperm, off_qcn;
   size_t off_rprev, off_w, off_tau, off_beta;      // QR sweep
   size_t off_mat, off_u, off_us, off_sig, off_perm;  // SVD sweep (aliases QR)
   size_t off_sites;
@@ -77,6 +77,7 @@ GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, size_t rb,
   size_t o = 0;
   p.off_chi = o;   o = align_up(o + sizeof(int) * (kMaxN + 2), 16);
   p.off_qb = o;    o = align_up(o + sizeof(int) * (kMaxN + 2), 16);
+  p.off_soff = o;  o = align_up(o + sizeof(int) * (kMaxN + 2), 16);   // slot offsets
   p.off_terms = o; o = align_up(o + (sizeof(unsigned long long) + sizeof(int) + cb + 8) * (M + 2), 16);
   p.off_amps = o;  o = align_up(o + cb * (M + 2), 16);
   p.off_misc = o;  o = align_up(o + 512, 16);

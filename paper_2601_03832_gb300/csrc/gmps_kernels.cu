@@ -192,7 +192,7 @@ struct Blk {
   const InstDesc* d;
   int n;
   S* sites;                // slab base (shared or global)
-  const long long* off;    // slot offsets
+  const int* off;          // slot offsets (shared copy)
   int* chi;                // [n+1] bond after the last SVD sweep (shared)
   int* qb;                 // [n+1] bonds after the QR sweep (shared)
   unsigned long long* tbits;  // direct-sum product terms
@@ -213,7 +213,7 @@ struct Blk {
   int* misc;               // [0] status, [1] max sweeps, [2] sweeps sum, [3] svd count, [4] k kept
   double* dmisc;           // [0] log_norm, [1] discarded, [2..5] phase coefficients
   T* tmisc;                // [0] rank-rule eps, [1] tol, [2] discarded weight, [3..6] e^{i phi}-1 and 1-e^{i psi},
-                           // [7] 2^{-n/2}, [8] Jacobi skip floor
+                           // [7] 2^{-n/2}, [8] Jacobi skip floor, [9] squared norm of the swept matrices
   __device__ S* slot(int l) const { return sites + off[l]; }
 };
 
@@ -431,16 +431,18 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
       }
       const bool scl = K<T>::kScaleColumns && em > -2000;
       const T sc = scl ? pow2<T>(-em) : (T)1;
+      // the pivot column's norm (rows >= j) is cn[j] unless the column was rescaled
       T s = 0;
-      for (int i = j + threadIdx.x; i < m; i += G) {
-        cx<T> x = A[i * lda + j];
-        if (scl) {
-          x = cscale(x, sc);
+      if (scl) {
+        for (int i = j + threadIdx.x; i < m; i += G) {
+          cx<T> x = cscale(A[i * lda + j], sc);
           A[i * lda + j] = x;
+          s += abs2(x);
         }
-        s += abs2(x);
+        for (int o = G >> 1; o > 0; o >>= 1) s += shx_m(s, o, gmask);
+      } else {
+        s = cn[j];
       }
-      for (int o = G >> 1; o > 0; o >>= 1) s += shx_m(s, o, gmask);
       if (threadIdx.x == 0) {
         cx<T> x0 = A[j * lda + j];
         T a2 = abs2(x0);
@@ -607,6 +609,7 @@ __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu,
         cx<T> gg;
         gg.re = shidx(part, base + 2 * Q);
         gg.im = shidx(part, base + 3 * Q);
+        // skip pairs with a row below the noise floor (dropped by the rank rule)
         if (act && a > skip2 && b > skip2) {
           const int sh = expo_of(a > b ? a : b);
           const float af = f32_scaled(a, sh), bf = f32_scaled(b, sh);
@@ -930,19 +933,18 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     __syncthreads();
     PROF_MARK(5);
     // noise floor for skipping rotations: (max(m,n) eps / 4)^2 times the
-    // largest squared row norm
-    if (threadIdx.x < 32) {
-      T amax = 0;
-      for (int i = threadIdx.x; i < rl; i += 32) {
-        T s2 = 0;
-        for (int j = 0; j < c; ++j) s2 += abs2(B.Mat[i * c + j]);
-        amax = fmax(amax, s2);
-      }
-      for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, shx(amax, o));
-      if (threadIdx.x == 0) {
-        const T f = (T)max(rl, c) * eps_rule * (T)0.25f;
-        B.tmisc[8] = amax * f * f;
-      }
+    // squared Frobenius norm of the matrix, which the sweep conserves up to
+    // truncation -- measured once, at its first site
+    if (l == n - 1 && threadIdx.x < 32) {
+      T f2 = 0;
+      for (int e = threadIdx.x; e < rl * c; e += 32) f2 += abs2(B.Mat[e]);
+      f2 = gsum(f2, 32);
+      if (threadIdx.x == 0) B.tmisc[9] = f2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const T f = (T)max(rl, c) * eps_rule * (T)0.25f;
+      B.tmisc[8] = B.tmisc[9] * f * f;
     }
     __syncthreads();
     PROF_MARK(6);
@@ -958,7 +960,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
         if (i < rl)
           for (int j = g.lg; j < c; j += G) s2 += abs2(B.Mat[i * c + j]);
         s2 = gsum(s2, G);
-        if (i < rl && g.lg == 0) B.sig[i] = sqrt(s2);
+        if (i < rl && g.lg == 0) B.sig[i] = s2;  // sigma_i^2 (rows are orthogonal)
       }
     }
     __syncthreads();
@@ -978,14 +980,16 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       B.misc[1] = max(B.misc[1], swc);
       B.misc[2] += swc;
       B.misc[3] += 1;
+      // sigma_t > max(tol, max(m,n) eps) sigma_0, compared as squares
       const T s0 = B.sig[B.perm[0]];
-      const T thr = fmax(tol_rule * s0, (T)max(rl, c) * eps_rule * s0);
+      const T fr = fmax(tol_rule, (T)max(rl, c) * eps_rule);
+      const T thr2 = fr * fr * s0;
       int k = 0;
       T tot = 0, kept = 0;
       for (int t = 0; t < rl; ++t) {
         const T st_ = B.sig[B.perm[t]];
-        tot += st_ * st_;
-        if (st_ > thr) ++k;
+        tot += st_;
+        if (st_ > thr2) ++k;
       }
       if (k < 1) k = 1;
       if (k > d.chi_max) k = d.chi_max;
@@ -993,10 +997,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
         set_status<T>(B.misc, kDevCapacity);
         k = d.chicap;
       }
-      for (int t = 0; t < k; ++t) {
-        const T st_ = B.sig[B.perm[t]];
-        kept += st_ * st_;
-      }
+      for (int t = 0; t < k; ++t) kept += B.sig[B.perm[t]];
       if (tot > (T)0 && kept != tot) B.tmisc[2] += (tot - kept) / tot;
       B.misc[4] = k;
     }
@@ -1014,12 +1015,14 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     __syncthreads();
 #endif
     // new site l = rows of V^dag (k x 2 x kr); US_l = U^dag[:, perm] * sigma (rl x k)
+    // 1/sigma of each kept row from one rsqrt of sigma^2 (qcn is free here)
+    for (int t = threadIdx.x; t < k; t += blockDim.x) B.qcn[t] = rsqrt(B.sig[B.perm[t]]);
     S* dst = B.slot(l);
+    __syncthreads();
     for (int e = threadIdx.x; e < k * c; e += blockDim.x) {
       const int t = e / c, j = e % c;
       const int pr = B.perm[t];
-      const T inv = (T)1 / B.sig[pr];
-      st(dst + e, cscale(B.Mat[pr * c + j], inv));
+      st(dst + e, cscale(B.Mat[pr * c + j], B.qcn[t]));
     }
     // U S with U = J^dag (the product of the rotations is accumulated in B.U;
     // the previous US was consumed when Mat was formed)
@@ -1027,7 +1030,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       const int i = e / k, t = e % k;
       const int pr = B.perm[t];
       const cx<T> u = B.U[pr * rl + i];
-      B.US[e] = cscale(mk<T>(u.re, -u.im), B.sig[pr]);
+      B.US[e] = cscale(mk<T>(u.re, -u.im), B.sig[pr] * B.qcn[t]);  // sigma = sigma^2 / sigma
     }
     if (threadIdx.x == 0) B.chi[l] = k;
     __syncthreads();
@@ -1160,7 +1163,11 @@ __global__ void __launch_bounds__(1024) iterate_kernel(const InstDesc* descs, in
     Blk<T, S> B;
     B.d = &d;
     B.n = n;
-    B.off = d.site_off;
+    {
+      int* so = (int*)(smem + P.off_soff);
+      for (int l = threadIdx.x; l <= n; l += blockDim.x) so[l] = (int)d.site_off[l];
+      B.off = so;
+    }
     B.chi = (int*)(smem + P.off_chi);
     B.qb = (int*)(smem + P.off_qb);
     unsigned char* tb = smem + P.off_terms;
@@ -1345,7 +1352,11 @@ __global__ void __launch_bounds__(1024) adjoint_kernel(const InstDesc* descs, co
   Blk<T, S> B;
   B.d = &d;
   B.n = n;
-  B.off = d.site_off;
+  {
+    int* so = (int*)(smem + P.off_soff);
+    for (int l = threadIdx.x; l <= n; l += blockDim.x) so[l] = (int)d.site_off[l];
+    B.off = so;
+  }
   B.chi = (int*)(smem + P.off_chi);
   B.qb = (int*)(smem + P.off_qb);
   unsigned char* tb = smem + P.off_terms;
