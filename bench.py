@@ -143,6 +143,84 @@ print(json.dumps({{"iters": done, "seconds": dt}}))
                       f"({APPLY} contraction, NumPy FP64, OMP_NUM_THREADS=1), {res['seconds']:.1f} s"}
 
 
+def extra_workloads(B, inputs, sptr, kslice_batch=100):
+    """Other forms and workloads, each measured once outside the headline's
+    timed region (CUDA events on the handle's stream)."""
+    import numpy as np
+    import torch
+
+    from oracle import reduced
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1000.0, r
+
+    # precision forms at the full n = 29 workload (P error vs the closed form)
+    inst = inputs.config_n29()
+    Pc = reduced.closed_form(inst.n, inst.M, inst.k)[0]
+    for dt in ("c64", "dw"):
+        g = B.GroverMPS(inst.n, inst.marked, dtype=dt, apply=APPLY, chi_max=inst.chi_max, stream=sptr)
+        sec, _ = timed(lambda: g.iterate(inst.k))
+        p = g.prob_marked()
+        bits = g.sample(4096, SAMPLE_SEED)
+        out[f"n29_{dt}"] = {"iterations_per_s": inst.k / sec, "P_marked": p, "P_err": p - Pc,
+                            "shots_4096_marked": int(np.sum(bits == inst.marked[0])),
+                            "dtype": {"c64": "c64 (FP64 QR/SVD)", "dw": "f32x2 double-word"}[dt]}
+        g.close()
+    # batched: 512 instances, k_i capped for a bounded measurement
+    from paper_2601_03832_gb300 import autotune
+    insts = inputs.config_batched(count=512)
+    for i in insts:
+        i.k = min(i.k, kslice_batch)
+    thr, rec = autotune.tune_batch(insts, dtype="c64", apply=APPLY, kslice=10, stream=sptr)
+    bt = B.GroverBatch(insts, dtype="c64", apply=APPLY, stream=sptr)
+    bt.set_threads(thr)
+    bt.run(use_graph=True)
+    bt.result()
+    sec, _ = timed(lambda: bt.run(use_graph=True))
+    p, st, rc = bt.result()
+    errs = [abs(p[i] - reduced.closed_form(x.n, x.M, x.k)[0]) for i, x in enumerate(insts)]
+    tot = sum(x.k for x in insts)
+    out["batched_512_c64"] = {"iterations_per_s": tot / sec, "seconds": sec, "total_iterations": tot,
+                              "k_cap": kslice_batch, "threads": thr, "autotune": rec, "graph": True,
+                              "max_P_err": max(errs), "median_P_err": float(np.median(errs)),
+                              "instances_with_status": int((st != 0).sum())}
+    bt.close()
+    # multi-marked n = 40, M = 32 (short slice)
+    mi = inputs.config_multi_marked(k=5)
+    g = B.GroverMPS(mi.n, mi.marked, dtype="c128", apply=APPLY, chi_max=mi.chi_max, tol=mi.tol, stream=sptr)
+    g.iterate(1)
+    sec, _ = timed(lambda: g.iterate(4))
+    p = g.prob_marked()
+    Pm = reduced.closed_form(mi.n, mi.M, 5)[0]
+    out["n40_M32_c128"] = {"iterations_per_s": 4 / sec, "k_slice": 5, "P_rel_err": (p - Pm) / Pm,
+                           "max_bond": g.stats()["max_bond"]}
+    g.close()
+    # differentiable: n = 20, M = 4, K = 64, 8 of the 64 phase vectors
+    di, phi, psi = inputs.config_differentiable(B=8)
+    worst = 0.0
+    t0 = time.perf_counter()
+    for b in range(8):
+        g = B.GroverMPS(di.n, di.marked, apply="split", chi_max=di.M + 1, differentiable=True,
+                        checkpoint_every=8, max_iters=di.k, stream=sptr)
+        g.iterate(di.k, phi[b], psi[b])
+        gphi, gpsi = g.backward(-1.0)
+        L, rphi, rpsi = reduced.loss_and_grad(di.n, di.M, phi[b], psi[b])
+        worst = max(worst, float(np.abs(gphi - rphi).max()), float(np.abs(gpsi - rpsi).max()))
+        g.close()
+    sec = time.perf_counter() - t0
+    out["differentiable_n20_M4_K64"] = {"fwd_bwd_ms_per_vector": 1000 * sec / 8, "vectors": 8,
+                                        "max_grad_err_vs_reduced_model": worst}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -174,6 +252,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other forms and workloads")
     ap.add_argument("--k", type=int, default=K_ITERS, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -295,6 +374,8 @@ def main():
     }
     clk_sum = clk.summary()
     line["clocks"] = clk_sum
+    if not args.no_extras and ws == 1:
+        line["workloads"] = extra_workloads(B, inputs, sptr)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     g.close()

@@ -99,7 +99,11 @@ static gmps_status validate(const gmps_config* c) {
 static gmps_status make_plan_for(const gmps_config* c, bool allow_resident, Plan* P) {
   const int smax = max_smem_optin();
   const size_t eb = storage_bytes(c->dtype), rb = linalg_real_bytes(c->dtype);
-  for (int slack = 2; slack >= 0; slack -= 2) {
+  // bond capacity: the exact rank bound M+1 plus headroom for rounding-noise
+  // singular values above the rank rule (larger for complex64's FP32 noise)
+  const int slacks[3] = {c->dtype == GMPS_C64_F64SVD ? c->M + 1 : 2, 2, 0};
+  for (int si = 0; si < 3; ++si) {
+    const int slack = slacks[si];
     int chicap = std::min(c->chi_max, c->M + 1 + slack);
     // a bond never exceeds 2^floor(n/2)
     long long half = 1;
