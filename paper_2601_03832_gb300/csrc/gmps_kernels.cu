@@ -126,6 +126,9 @@ struct K<double> {
   static __device__ __forceinline__ float jtolf() { return 1.7763568e-15f; }
   // squared column norm below which a Householder column counts as zero
   static __device__ __forceinline__ double tiny2() { return 0.0; }
+  // |x0|^2 <= phase_floor |x|^2: the pivot is negligible, its phase is taken as 1
+  // (keeps |x0|^2 out of the denormal range, where rsqrt is inaccurate)
+  static __device__ __forceinline__ double phase_floor() { return 7.52316384526264e-37; }  // 2^-120
   // Householder columns are scaled by a power of two first (needed only when
   // the exponent range is FP32's)
   static constexpr bool kScaleColumns = false;
@@ -136,6 +139,7 @@ struct K<float> {
   static __device__ __forceinline__ float jtol() { return 8.f * 1.1920929e-07f; }
   static __device__ __forceinline__ float jtolf() { return 9.536743e-07f; }
   static __device__ __forceinline__ float tiny2() { return 0.f; }
+  static __device__ __forceinline__ float phase_floor() { return 8.6736174e-19f; }  // 2^-60
   static constexpr bool kScaleColumns = true;
 };
 template <>
@@ -144,6 +148,7 @@ struct K<dw> {
   static __device__ __forceinline__ dw jtol() { return dw(5.6843419e-14f); }  // 2^-44
   static __device__ __forceinline__ float jtolf() { return 5.6843419e-14f; }
   static __device__ __forceinline__ dw tiny2() { return dw(0.f); }
+  static __device__ __forceinline__ dw phase_floor() { return dw(7.8886091e-31f); }  // 2^-100
   // squares of entries below ~1e-16 are FP32 denormals: the reflector is built
   // from the column scaled to O(1) by an exact power of two
   static constexpr bool kScaleColumns = true;
@@ -314,7 +319,7 @@ __device__ void qr_householder(cx<T>* A, int m, int ncol, int lda, T* tau, cx<T>
           T nrm = s * inv;
           cx<T> ph = mk<T>(1, 0);
           T ax0 = 0;
-          if (a2 > 0) {
+          if (a2 > K<T>::phase_floor() * s) {
             T ia = rsqrt(a2);
             ax0 = a2 * ia;
             ph = cscale(x0, ia);
@@ -379,6 +384,17 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
   T floor2 = 0;
   int rank = pmax;
   for (int j = 0; j < pmax; ++j) {
+#ifdef GMPS_CHECK
+    if (threadIdx.x == 0) {
+      for (int c = j; c < ncol; ++c) {
+        double a = 0;
+        for (int i = j; i < m; ++i) a += (double)abs2(A[i * lda + c]);
+        if (fabs(a - (double)cn[c]) > 1e-12 * (1.0 + a))
+          printf("CNCHECK m=%d ncol=%d j=%d c=%d cn=%.15e actual=%.15e\n", m, ncol, j, c, (double)cn[c], a);
+      }
+    }
+    __syncthreads();
+#endif
     if (threadIdx.x == 0) {
       // pivot: largest remaining norm (compared through exact FP32 images)
       int best = j;
@@ -448,12 +464,21 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
         T a2 = abs2(x0);
         cx<T> b = mk<T>(0, 0);
         T t = 0;
+#ifdef GMPS_CHECK
+        {
+          double a = 0;
+          for (int i = j; i < m; ++i) a += (double)abs2(A[i * lda + j]);
+          if (fabs(a - (double)s) > 1e-12 * (1.0 + a))
+            printf("HHCHECK j=%d s=%.15e actual=%.15e x0=(%.6e,%.6e)\n", j, (double)s, a, (double)x0.re,
+                   (double)x0.im);
+        }
+#endif
         if (s > K<T>::tiny2()) {
           T inv = rsqrt(s);
           T nrm = s * inv;
           cx<T> ph = mk<T>(1, 0);
           T ax0 = 0;
-          if (a2 > 0) {
+          if (a2 > K<T>::phase_floor() * s) {
             T ia = rsqrt(a2);
             ax0 = a2 * ia;
             ph = cscale(x0, ia);
@@ -491,6 +516,18 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
       if (act && g.lg == 0) cn[c] = s2;
     }
     __syncthreads();
+#ifdef GMPS_CHECK
+    if (threadIdx.x == 0) {
+      for (int jj = 0; jj <= j; ++jj) {
+        double v2 = 0;
+        for (int i = jj; i < m; ++i) v2 += (double)abs2(A[i * lda + jj]);
+        const double t = (double)tau[jj];
+        if (t != 0.0 && fabs(v2 * t - 2.0) > 1e-10)
+          printf("STEPCHECK after step %d: reflector %d off (%.12f) best=%d\n", j, jj, v2 * t, ctl[0]);
+      }
+    }
+    __syncthreads();
+#endif
   }
   return rank;
 }
@@ -843,6 +880,19 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       p = qr_rank_revealing<T>(B.W, m, xr, xr, B.tau, B.beta, B.qperm, B.qcn, B.misc + 8, fl * fl);
     }
     if (p < 1) p = 1;
+#ifdef GMPS_CHECK
+    if (threadIdx.x == 0) {
+      for (int jj = 0; jj < p; ++jj) {
+        double v2 = 0;
+        for (int i = jj; i < m; ++i) v2 += (double)abs2(B.W[i * xr + jj]);
+        const double t = (double)B.tau[jj];
+        if (t != 0.0 && fabs(v2 * t - 2.0) > 1e-10)
+          printf("REFLCHECK l=%d m=%d xr=%d j=%d |v|^2*tau=%.12f tau=%.6e |beta|=%.6e\n", l, m, xr, jj, v2 * t, t,
+                 sqrt((double)abs2(B.beta[jj])));
+      }
+    }
+    __syncthreads();
+#endif
     PROF_MARK(1);
     // R P^T -> Rp (p x xr, ld xr): column c of the pivoted R is original column perm[c]
     for (int e = threadIdx.x; e < p * xr; e += blockDim.x) {
@@ -948,6 +998,12 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     }
     __syncthreads();
     PROF_MARK(6);
+#ifdef GMPS_CHECK
+    __shared__ double2 chkM[48 * 48];
+    for (int e = threadIdx.x; e < rl * c && e < 48 * 48; e += blockDim.x)
+      chkM[e] = make_double2((double)B.Mat[e].re, (double)B.Mat[e].im);
+    __syncthreads();
+#endif
     const int sw = jacobi_rows<T>(B.Mat, rl, c, c, B.U, rl, d.max_sweeps, K<T>::jtolf(), B.tmisc[8]);
     PROF_MARK(7);
     // row norms -> sigma, ranks -> perm
@@ -1056,8 +1112,8 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
             re += (double)u.re * (double)v.re - (double)u.im * (double)v.im;
             im += (double)u.re * (double)v.im + (double)u.im * (double)v.re;
           }
-          (void)re;
-          (void)im;
+          if (rl * c <= 48 * 48)
+            er = fmax(er, fabs(re - chkM[i * c + j].x) + fabs(im - chkM[i * c + j].y));
         }
       if (eo > 1e-12 || er > 1e-12) {
         printf("SVDCHECK l=%d rl=%d c=%d k=%d sw=%d orth=%.3e recon=%.3e sig:", l, rl, c, k, sw, eo, er);

@@ -197,3 +197,18 @@ def test_batched_small(B):
     b.run(use_graph=True)
     p2, _, _ = b.result()
     assert np.array_equal(p, p2)
+
+
+def test_batched_many_marked_fp64_all_instances(B):
+    """128 instances of the batched workload (n in [16, 36], M in [1, 16], k_i
+    capped at 100) in FP64: every P_marked within 1e-10 of the closed form.
+    Includes pivots whose squared modulus is a denormal double (n = 17, M = 12)."""
+    insts = inputs.config_batched(count=128)
+    for i in insts:
+        i.k = min(i.k, 100)
+    b = B.GroverBatch(insts, dtype="c128", apply="fused")
+    b.run(use_graph=False)
+    p, st, rc = b.result()
+    assert rc == 0 and not st.any()
+    errs = [abs(p[i] - reduced.closed_form(x.n, x.M, x.k)[0]) for i, x in enumerate(insts)]
+    assert max(errs) < TOL_P_F64, (int(np.argmax(errs)), max(errs))
