@@ -221,6 +221,24 @@ def extra_workloads(B, inputs, sptr, kslice_batch=100):
     return out
 
 
+def batch_probe(count: int, kcap: int):
+    """One batched launch of the first `count` instances of the batched
+    workload with k_i capped at `kcap` (a small case for ncu captures)."""
+    import torch
+
+    from paper_2601_03832_gb300 import binding as B
+    from paper_2601_03832_gb300 import inputs
+    torch.cuda.set_device(0)
+    insts = inputs.config_batched(count=512)[:count]
+    for i in insts:
+        i.k = min(i.k, kcap)
+    b = B.GroverBatch(insts, dtype="c64", apply=APPLY)
+    b.set_threads(256)
+    b.run(use_graph=False)
+    p, st, rc = b.result()
+    print(json.dumps({"batch_probe": count, "k_cap": kcap, "status": int(rc), "instances_with_status": int((st != 0).sum())}))
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -254,9 +272,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other forms and workloads")
     ap.add_argument("--k", type=int, default=K_ITERS, help=argparse.SUPPRESS)
+    ap.add_argument("--batch-probe", default=None, metavar="COUNT,KCAP",
+                    help="run one batched launch (complex64, fused, 256 threads) and exit (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_probe:
+        return batch_probe(*[int(x) for x in args.batch_probe.split(",")])
 
     import numpy as np
     import torch

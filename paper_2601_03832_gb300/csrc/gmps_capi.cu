@@ -90,8 +90,8 @@ static gmps_status validate(const gmps_config* c) {
   if (c->dtype != GMPS_C128 && c->dtype != GMPS_C64_F64SVD && c->dtype != GMPS_DW)
     return fail(GMPS_ERR_ARG, "unknown dtype");
   if (c->apply < 0 || c->apply > 2) return fail(GMPS_ERR_ARG, "apply must be 0, 1 or 2");
-  if (c->threads != 0 && (c->threads % 32 != 0 || c->threads < 32 || c->threads > 1024))
-    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+  if (c->threads != 0 && (c->threads % 32 != 0 || c->threads < 32 || c->threads > 512))
+    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
   if (c->max_sweeps < 0) return fail(GMPS_ERR_ARG, "max_sweeps must be >= 0");
   return GMPS_OK;
 }
@@ -819,8 +819,8 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
 
 gmps_status grover_mps_batch_set_threads(gmps_batch_handle b, int threads) {
   if (!b) return fail(GMPS_ERR_ARG, "NULL handle");
-  if (threads != 0 && (threads % 32 || threads < 32 || threads > 1024))
-    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+  if (threads != 0 && (threads % 32 || threads < 32 || threads > 512))
+    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
   int maxx = 1;
   for (auto& P : b->plans) maxx = std::max(maxx, P.xcap);
   b->threads = threads ? threads : auto_threads(maxx);

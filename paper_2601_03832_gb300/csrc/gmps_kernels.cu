@@ -1201,7 +1201,7 @@ __device__ void chain_targets(Blk<T, S>& B, int nt) {
 
 // ------------------------------------------------------------ the kernel
 template <class T, class S, class CR>
-__global__ void __launch_bounds__(1024) iterate_kernel(const InstDesc* descs, int count, int* queue) {
+__global__ void __launch_bounds__(512) iterate_kernel(const InstDesc* descs, int count, int* queue) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_idx;
   for (;;) {
@@ -1397,7 +1397,7 @@ __global__ void __launch_bounds__(1024) iterate_kernel(const InstDesc* descs, in
 // the forward chain's marked amplitudes and <s|psi_{k-1}> for k-1 = k_lo..k_hi-1.
 // The gradients are written scaled by `scale` (dL/dP).
 template <class T, class S, class CR>
-__global__ void __launch_bounds__(1024) adjoint_kernel(const InstDesc* descs, const double* rec, long long k_lo,
+__global__ void __launch_bounds__(512) adjoint_kernel(const InstDesc* descs, const double* rec, long long k_lo,
                                                        long long k_hi, const double* phi, const double* psi,
                                                        double scale, double* gphi, double* gpsi, int project) {
   extern __shared__ __align__(16) unsigned char smem[];
