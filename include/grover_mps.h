@@ -100,7 +100,7 @@ typedef struct gmps_config {
   int chi_max;              /* bond cap, >= 1 */
   double tol;               /* relative SVD truncation tolerance, >= 0 */
   int max_sweeps;           /* Jacobi sweep limit per SVD; 0 = default 40 */
-  int threads;              /* CTA size (multiple of 32, <= 512); 0 = auto */
+  int threads;              /* CTA size (multiple of 32, <= 256); 0 = auto */
   int differentiable;       /* keep checkpoints for grover_mps_backward */
   int checkpoint_every;     /* iterations between checkpoints; 0 = 8 */
   int max_iters;            /* differentiable: max total iterations kept */

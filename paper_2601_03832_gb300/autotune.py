@@ -19,7 +19,7 @@ from . import binding
 
 CACHE = os.environ.get("GMPS_TUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json"))
-CANDIDATES = (64, 128, 256, 512)
+CANDIDATES = (64, 128, 256)
 
 
 def _key(insts, dtype, apply):

@@ -41,14 +41,16 @@ static gmps_status cuda_fail(cudaError_t e, const char* where) {
 
 static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
-// eps of the rank rule sigma_i > max(tol, max(m,n) eps) sigma_0: the unit of
-// the storage precision (FP32 for complex64, FP64), and for double-word the
-// accumulated rounding of a QR + Jacobi chain, 2^-42, so that rounding noise
-// is never kept as a Schmidt direction.
+// eps of the rank rule sigma_i > max(tol, max(m,n) eps) sigma_0, set above
+// the rounding noise that a contraction + QR + Jacobi chain leaves in a
+// rank-deficient direction, so that the noise is never kept as a Schmidt
+// direction: FP32's unit for complex64, 2^-42 for double-word, and four FP64
+// units (2^-50) for FP64 -- a noise row of 2.7 units was measured on a 2 x 2
+// step, whose max(m,n) = 2 would otherwise put the threshold at 2 units.
 static double trunc_eps_for(int dtype) {
   if (dtype == GMPS_C64_F64SVD) return 1.1920928955078125e-07;
   if (dtype == GMPS_DW) return 2.2737367544323206e-13;
-  return 2.220446049250313e-16;
+  return 8.881784197001252e-16;
 }
 
 // ---------------------------------------------------------------- sizing
@@ -68,8 +70,7 @@ static int auto_threads(int xcap) {
   if (xcap <= 8) return 32;
   if (xcap <= 16) return 64;
   if (xcap <= 32) return 128;
-  if (xcap <= 64) return 256;
-  return 512;
+  return 256;
 }
 
 static gmps_status validate(const gmps_config* c) {
@@ -90,8 +91,8 @@ static gmps_status validate(const gmps_config* c) {
   if (c->dtype != GMPS_C128 && c->dtype != GMPS_C64_F64SVD && c->dtype != GMPS_DW)
     return fail(GMPS_ERR_ARG, "unknown dtype");
   if (c->apply < 0 || c->apply > 2) return fail(GMPS_ERR_ARG, "apply must be 0, 1 or 2");
-  if (c->threads != 0 && (c->threads % 32 != 0 || c->threads < 32 || c->threads > 512))
-    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
+  if (c->threads != 0 && (c->threads % 32 != 0 || c->threads < 32 || c->threads > 256))
+    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 256]");
   if (c->max_sweeps < 0) return fail(GMPS_ERR_ARG, "max_sweeps must be >= 0");
   return GMPS_OK;
 }
@@ -819,8 +820,8 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
 
 gmps_status grover_mps_batch_set_threads(gmps_batch_handle b, int threads) {
   if (!b) return fail(GMPS_ERR_ARG, "NULL handle");
-  if (threads != 0 && (threads % 32 || threads < 32 || threads > 512))
-    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 512]");
+  if (threads != 0 && (threads % 32 || threads < 32 || threads > 256))
+    return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 256]");
   int maxx = 1;
   for (auto& P : b->plans) maxx = std::max(maxx, P.xcap);
   b->threads = threads ? threads : auto_threads(maxx);

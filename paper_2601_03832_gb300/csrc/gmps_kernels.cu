@@ -575,6 +575,63 @@ __device__ void qr_form_q(cx<T>* A, int m, int p, int lda, const T* tau) {
   }
 }
 
+// a > b (and a == b) for non-negative values; doubles compare through their
+// bit patterns (an integer compare, off the FP64 pipe)
+template <class T>
+__device__ __forceinline__ bool nn_gt(T a, T b) {
+  return a > b;
+}
+template <>
+__device__ __forceinline__ bool nn_gt<double>(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+template <class T>
+__device__ __forceinline__ bool nn_eq(T a, T b) {
+  return a == b;
+}
+template <>
+__device__ __forceinline__ bool nn_eq<double>(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+// Plane rotation for one Jacobi pair from its Gram entries a = |x_p|^2,
+// b = |x_q|^2 and g = <x_p, x_q>: the classical angle (Rutishauser: zeta =
+// (b - a)/(2|g|), t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2))) computed in FP32
+// from exact power-of-two-scaled images of the T-precision entries, then
+// normalised in T.  Returns false when the pair is left alone (a row below the
+// noise floor skip2, the pair orthogonal to tolf, or a degenerate angle); else
+// cc = cos and (sre, sim) = sin * g/|g|, with cc^2 + |s|^2 = 1 to T's rounding.
+// The angle is kept to IEEE FP32 accuracy (not MUFU estimates): a sloppier
+// angle costs extra rotations, whose rounding lifts the noise rows of
+// rank-deficient matrices toward the rank rule's threshold.
+template <class T>
+__device__ __forceinline__ bool jacobi_rotation(T a, T b, cx<T> gg, float tolf, T skip2, T& cc, T& sre, T& sim) {
+  if (!(nn_gt(a, skip2) && nn_gt(b, skip2))) return false;
+  const int sh = expo_of(nn_gt(a, b) ? a : b);
+  const float af = f32_scaled(a, sh), bf = f32_scaled(b, sh);
+  const float dab = f32_scaled(b - a, sh);  // difference taken in T
+  const float gr = f32_scaled(gg.re, sh), gi = f32_scaled(gg.im, sh);
+  const float gabs = sqrtf(fmaf(gr, gr, gi * gi));
+  if (!(gabs > tolf * sqrtf(af) * sqrtf(bf) && gabs > 0.f)) return false;
+  const float zeta = dab / (2.f * gabs);
+  // small-root formula; for |zeta| > 2^60 (zeta^2 would overflow) t = 1/(2 zeta)
+  const float tt = fabsf(zeta) > 1.1529215e18f ? 0.5f / zeta
+                                               : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+  if (!(tt != 0.f && isfinite(tt))) return false;
+  const float cf = rsqrtf(fmaf(tt, tt, 1.f));
+  const float sf = cf * tt;
+  cc = widen<T>(cf);
+  sre = widen<T>(sf * (gr / gabs));
+  sim = widen<T>(sf * (gi / gabs));
+  const T rho = fma(cc, cc, fma(sre, sre, sim * sim));
+  const T dd = rho - (T)1;
+  const T f = fma(dd, fma(dd, (T)0.375f, (T)-0.5f), (T)1);
+  cc *= f;
+  sre *= f;
+  sim *= f;
+  return true;
+}
+
 // ---------------------------------------------------- one-sided Jacobi SVD
 // Orthogonalise the rows of Mat (r x c, leading dim ldm) by unitary plane
 // rotations J = [[c, -conj(s)], [s, c]] applied from the left (Hestenes'
@@ -647,55 +704,35 @@ __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu,
         gg.re = shidx(part, base + 2 * Q);
         gg.im = shidx(part, base + 3 * Q);
         // skip pairs with a row below the noise floor (dropped by the rank rule)
-        if (act && a > skip2 && b > skip2) {
-          const int sh = expo_of(a > b ? a : b);
-          const float af = f32_scaled(a, sh), bf = f32_scaled(b, sh);
-          const float dab = f32_scaled(b - a, sh);  // difference taken in T
-          const float gr = f32_scaled(gg.re, sh), gi = f32_scaled(gg.im, sh);
-          const float gabs = sqrtf(fmaf(gr, gr, gi * gi));
-          if (gabs > tolf * sqrtf(af) * sqrtf(bf) && gabs > 0.f) {
-            const float zeta = dab / (2.f * gabs);
-            // small-root formula; for |zeta| > 2^60 (zeta^2 would overflow) t = 1/(2 zeta)
-            const float tt = fabsf(zeta) > 1.1529215e18f
-                                 ? 0.5f / zeta
-                                 : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-            if (tt != 0.f && isfinite(tt)) {
-              const float cf = rsqrtf(fmaf(tt, tt, 1.f));
-              const float sf = cf * tt;
-              T cc = widen<T>(cf), sre = widen<T>(sf * (gr / gabs)), sim = widen<T>(sf * (gi / gabs));
-              const T rho = fma(cc, cc, fma(sre, sre, sim * sim));
-              const T dd = rho - (T)1;
-              const T f = fma(dd, fma(dd, (T)0.375f, (T)-0.5f), (T)1);
-              cc *= f;
-              // row p: c x_p - conj(s) x_q ; row q: c x_q + s x_p
-              const bool rowp = (quarter & 1) == 0;
-              const cx<T> coef = rowp ? mk<T>(-sre * f, sim * f) : mk<T>(sre * f, sim * f);
-              cx<T>* base_ptr = quarter < 2 ? Mat : U;
-              const int ld = quarter < 2 ? ldm : ldu;
-              const int len = quarter < 2 ? c : r;
-              const int own = rowp ? p : q, oth = rowp ? q : p;
-              // blocks of 4Q columns; the block loop's trip count depends only on
-              // max(c, r) and Q (team-uniform), so every lane of the team reaches
-              // each sync; lanes past their row length only guard their accesses
-              const int span = max(c, r);
-              for (int jb = 0; jb < span; jb += 4 * Q) {
-                cx<T> nv[4];
+        T cc, sre, sim;
+        if (act && jacobi_rotation<T>(a, b, gg, tolf, skip2, cc, sre, sim)) {
+          // row p: c x_p - conj(s) x_q ; row q: c x_q + s x_p
+          const bool rowp = (quarter & 1) == 0;
+          const cx<T> coef = rowp ? mk<T>(-sre, sim) : mk<T>(sre, sim);
+          cx<T>* base_ptr = quarter < 2 ? Mat : U;
+          const int ld = quarter < 2 ? ldm : ldu;
+          const int len = quarter < 2 ? c : r;
+          const int own = rowp ? p : q, oth = rowp ? q : p;
+          // blocks of 4Q columns; the block loop's trip count depends only on
+          // max(c, r) and Q (team-uniform), so every lane of the team reaches
+          // each sync; lanes past their row length only guard their accesses
+          const int span = max(c, r);
+          for (int jb = 0; jb < span; jb += 4 * Q) {
+            cx<T> nv[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  const int j = jb + u * Q + ql;
-                  if (j < len) nv[u] = cmac(cscale(base_ptr[own * ld + j], cc), coef, base_ptr[oth * ld + j]);
-                }
-                __syncwarp(tmask);  // both rows read before either is written
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                  const int j = jb + u * Q + ql;
-                  if (j < len) base_ptr[own * ld + j] = nv[u];
-                }
-                __syncwarp(tmask);
-              }
-              rotated = 1;
+            for (int u = 0; u < 4; ++u) {
+              const int j = jb + u * Q + ql;
+              if (j < len) nv[u] = cmac(cscale(base_ptr[own * ld + j], cc), coef, base_ptr[oth * ld + j]);
             }
+            __syncwarp(tmask);  // both rows read before either is written
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int j = jb + u * Q + ql;
+              if (j < len) base_ptr[own * ld + j] = nv[u];
+            }
+            __syncwarp(tmask);
           }
+          rotated = 1;
         }
       }
       __syncthreads();
@@ -724,80 +761,82 @@ __device__ __forceinline__ CR mpo_w(int op, int b, int l, int s, int sp, const u
 // B_l is the operator-expanded site l: an MPO contraction (op 0 oracle, 1
 // diffusion; boundary vector `lbnd` of length D at site 0, all-ones at the
 // right end) or a direct sum of the current MPS (coefficient cpsi at site 0)
-// with `nt` product states (coefficients tcoef at site 0).
+// with `nt` product states (coefficients tcoef at site 0).  expand_elem gives
+// one element C[(i, s), j]; expand_absorb writes all of W with the block.
 template <class T, class S, class CR>
-__device__ void expand_absorb(Blk<T, S>& B, int l, int r, int xl, int xr, int mode, int op, int D,
-                              const cx<T>* lbnd, cx<T> cpsi, int nt) {
+__device__ __forceinline__ cx<T> expand_elem(Blk<T, S>& B, int l, int i, int s, int j, int xl, int mode, int op,
+                                             int D, const cx<T>* lbnd, cx<T> cpsi, int nt) {
   const int n = B.n;
   const int cl = B.chi[l], cr = B.chi[l + 1];
   const S* A = B.slot(l);
-  const int total = r * 2 * xr;
   const CR h = K<CR>::isq2();
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int i = e / (2 * xr);
-    const int s = (e / xr) & 1;
-    const int j = e % xr;
-    cx<CR> acc = mk<CR>(0, 0);
-    if (mode == 0) {  // ---- MPO
-      if (n == 1) {
-        for (int b = 0; b < D; ++b) {
-          cx<CR> tb = mk<CR>(0, 0);
-          for (int sp = 0; sp < 2; ++sp) {
-            const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
-            if (w != (CR)0) tb = cmac(tb, mk<CR>(w, 0), ld<CR>(A + sp));
-          }
-          acc = cmac(acc, cvt<CR>(lbnd[b]), tb);
-        }
-      } else if (l == 0) {
-        const int b = j / cr, jj = j % cr;
+  cx<CR> acc = mk<CR>(0, 0);
+  if (mode == 0) {  // ---- MPO
+    if (n == 1) {
+      for (int b = 0; b < D; ++b) {
         cx<CR> tb = mk<CR>(0, 0);
         for (int sp = 0; sp < 2; ++sp) {
           const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
-          if (w != (CR)0) tb = cmac(tb, mk<CR>(w, 0), ld<CR>(A + sp * cr + jj));
+          if (w != (CR)0) tb = cmac(tb, mk<CR>(w, 0), ld<CR>(A + sp));
         }
-        acc = cmul(cvt<CR>(lbnd[b]), tb);
-      } else {
-        const bool last = (l == n - 1);
-        const int b0 = last ? 0 : j / cr, b1 = last ? D : b0 + 1;
-        const int jj = last ? 0 : j % cr;
-        for (int b = b0; b < b1; ++b) {
-          for (int sp = 0; sp < 2; ++sp) {
-            const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
-            if (w == (CR)0) continue;
-            cx<CR> t = mk<CR>(0, 0);
-            for (int a = 0; a < cl; ++a)
-              t = cmac(t, cvt<CR>(B.Rp[i * xl + b * cl + a]), ld<CR>(A + (a * 2 + sp) * cr + jj));
-            acc = cmac(acc, mk<CR>(w, 0), t);
-          }
-        }
+        acc = cmac(acc, cvt<CR>(lbnd[b]), tb);
       }
-    } else {  // ---- direct sum
-      auto pval = [&](int t) -> CR {
-        if (B.tplus[t]) return h;
-        return ((int)((B.tbits[t] >> l) & 1ull) == s) ? (CR)1 : (CR)0;
-      };
-      if (n == 1) {
-        acc = cmul(cvt<CR>(cpsi), ld<CR>(A + s));
-        for (int t = 0; t < nt; ++t) acc = cmac(acc, cvt<CR>(B.tcoef[t]), mk<CR>(pval(t), 0));
-      } else if (l == 0) {
-        if (j < cr)
-          acc = cmul(cvt<CR>(cpsi), ld<CR>(A + s * cr + j));
-        else
-          acc = cscale(cvt<CR>(B.tcoef[j - cr]), pval(j - cr));
-      } else if (l == n - 1) {
-        for (int a = 0; a < cl; ++a) acc = cmac(acc, cvt<CR>(B.Rp[i * xl + a]), ld<CR>(A + a * 2 + s));
-        for (int t = 0; t < nt; ++t) acc = cmac(acc, cvt<CR>(B.Rp[i * xl + cl + t]), mk<CR>(pval(t), 0));
-      } else {
-        if (j < cr) {
+    } else if (l == 0) {
+      const int b = j / cr, jj = j % cr;
+      cx<CR> tb = mk<CR>(0, 0);
+      for (int sp = 0; sp < 2; ++sp) {
+        const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
+        if (w != (CR)0) tb = cmac(tb, mk<CR>(w, 0), ld<CR>(A + sp * cr + jj));
+      }
+      acc = cmul(cvt<CR>(lbnd[b]), tb);
+    } else {
+      const bool last = (l == n - 1);
+      const int b0 = last ? 0 : j / cr, b1 = last ? D : b0 + 1;
+      const int jj = last ? 0 : j % cr;
+      for (int b = b0; b < b1; ++b) {
+        for (int sp = 0; sp < 2; ++sp) {
+          const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
+          if (w == (CR)0) continue;
+          cx<CR> t = mk<CR>(0, 0);
           for (int a = 0; a < cl; ++a)
-            acc = cmac(acc, cvt<CR>(B.Rp[i * xl + a]), ld<CR>(A + (a * 2 + s) * cr + j));
-        } else {
-          acc = cscale(cvt<CR>(B.Rp[i * xl + cl + (j - cr)]), pval(j - cr));
+            t = cmac(t, cvt<CR>(B.Rp[i * xl + b * cl + a]), ld<CR>(A + (a * 2 + sp) * cr + jj));
+          acc = cmac(acc, mk<CR>(w, 0), t);
         }
       }
     }
-    B.W[e] = cvt<T>(acc);
+  } else {  // ---- direct sum
+    auto pval = [&](int t) -> CR {
+      if (B.tplus[t]) return h;
+      return ((int)((B.tbits[t] >> l) & 1ull) == s) ? (CR)1 : (CR)0;
+    };
+    if (n == 1) {
+      acc = cmul(cvt<CR>(cpsi), ld<CR>(A + s));
+      for (int t = 0; t < nt; ++t) acc = cmac(acc, cvt<CR>(B.tcoef[t]), mk<CR>(pval(t), 0));
+    } else if (l == 0) {
+      if (j < cr)
+        acc = cmul(cvt<CR>(cpsi), ld<CR>(A + s * cr + j));
+      else
+        acc = cscale(cvt<CR>(B.tcoef[j - cr]), pval(j - cr));
+    } else if (l == n - 1) {
+      for (int a = 0; a < cl; ++a) acc = cmac(acc, cvt<CR>(B.Rp[i * xl + a]), ld<CR>(A + a * 2 + s));
+      for (int t = 0; t < nt; ++t) acc = cmac(acc, cvt<CR>(B.Rp[i * xl + cl + t]), mk<CR>(pval(t), 0));
+    } else {
+      if (j < cr) {
+        for (int a = 0; a < cl; ++a)
+          acc = cmac(acc, cvt<CR>(B.Rp[i * xl + a]), ld<CR>(A + (a * 2 + s) * cr + j));
+      } else {
+        acc = cscale(cvt<CR>(B.Rp[i * xl + cl + (j - cr)]), pval(j - cr));
+      }
+    }
   }
+  return cvt<T>(acc);
+}
+template <class T, class S, class CR>
+__device__ void expand_absorb(Blk<T, S>& B, int l, int r, int xl, int xr, int mode, int op, int D,
+                              const cx<T>* lbnd, cx<T> cpsi, int nt) {
+  const int total = r * 2 * xr;
+  for (int e = threadIdx.x; e < total; e += blockDim.x)
+    B.W[e] = expand_elem<T, S, CR>(B, l, e / (2 * xr), (e / xr) & 1, e % xr, xl, mode, op, D, lbnd, cpsi, nt);
   __syncthreads();
 }
 
@@ -823,6 +862,8 @@ template <class T>
 __device__ __forceinline__ void set_status(int* misc, int code) {
   if (misc[0] == 0) misc[0] = code;
 }
+
+#include "gmps_tiny.cuh"
 
 // One contraction followed by the QR sweep and the truncated SVD sweep.
 template <class T, class S, class CR>
@@ -850,10 +891,25 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       __syncthreads();
       return;
     }
-    expand_absorb<T, S, CR>(B, l, r, xl, xr, mode, op, D, lbnd, cpsi, nt);
-    PROF_MARK(0);
     const int m = 2 * r;
     S* dst = B.slot(l);
+    if (l < n - 1 && m <= 8 && xr <= 4) {  // register-resident step (one warp)
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, c = lane >> 3, i = lane & 7;
+        const cx<T> w0 = (c < xr && i < m)
+                             ? expand_elem<T, S, CR>(B, l, i >> 1, i & 1, c, xl, mode, op, D, lbnd, cpsi, nt)
+                             : mk<T>(0, 0);
+        const T fl = (T)max(m, xr) * B.tmisc[0];
+        const int pt = tiny_qr<T, S>(w0, m, xr, fl * fl, dst, B.Rp);
+        if (threadIdx.x == 0) B.qb[l + 1] = pt;
+      }
+      __syncthreads();
+      PROF_MARK(1);
+      r = B.qb[l + 1];
+      continue;
+    }
+    expand_absorb<T, S, CR>(B, l, r, xl, xr, mode, op, D, lbnd, cpsi, nt);
+    PROF_MARK(0);
     if (l == n - 1) {
       for (int e = threadIdx.x; e < m; e += blockDim.x) st(dst + e, B.W[e]);
       if (threadIdx.x == 0) B.qb[n] = 1;
@@ -973,6 +1029,13 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     const int rl = B.qb[l], rr = B.qb[l + 1];
     const S* A = B.slot(l);
     const int c = 2 * kr;
+    if (rl <= 4 && c + rl <= 8) {  // register-resident step (one warp)
+      if (threadIdx.x < 32) tiny_svd_step<T, S, CR>(B, l, rl, rr, kr);
+      __syncthreads();
+      PROF_MARK(7);
+      kr = B.misc[4];
+      continue;
+    }
     // Mat = A (rl x 2 x rr) * US (rr x kr)  -> rl x (2 kr)
     for (int e = threadIdx.x; e < rl * c; e += blockDim.x) {
       const int i = e / c, s = (e / kr) & 1, j = e % kr;
@@ -1160,12 +1223,46 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
 }
 
 // <target_t|psi> for product-state targets (basis strings or |+>^n), by the
-// chain v <- v A_l[:, b_l, :] (or v (A_l[:,0,:]+A_l[:,1,:])/sqrt 2); one warp
-// per target, lanes over the right bond (<= 64).
+// chain v <- v A_l[:, b_l, :] (or v (A_l[:,0,:]+A_l[:,1,:])/sqrt 2); lanes
+// over the right bond: a group of G lanes per target when every bond fits
+// 16 lanes, else one warp per target (bonds <= 64).
 template <class T, class S, class CR>
 __device__ void chain_targets(Blk<T, S>& B, int nt) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const CR h = K<CR>::isq2();
+  const int G = pow2_cap32(B.d->chicap);  // lanes that cover any bond
+  if (G <= 16) {
+    // 32/G targets per warp in one instruction stream; for |+>^n the factor
+    // (A_0 + A_1) v is summed first and scaled by 1/sqrt 2 once per site
+    const int per = 32 / G, lg = lane & (G - 1), base = lane & ~(G - 1);
+    for (int t0 = warp * per; t0 < nt; t0 += nw * per) {
+      const int t = t0 + lane / G;
+      const bool on = t < nt;
+      const bool plus = on && B.tplus[t];
+      const unsigned long long bits = (on && !plus) ? B.tbits[t] : 0ull;
+      cx<CR> v = mk<CR>(lg == 0 ? (CR)1 : (CR)0, 0);
+      for (int l = 0; l < B.n; ++l) {
+        const int cl = B.chi[l], cr = B.chi[l + 1];
+        const S* A = B.slot(l);
+        const int b = (int)((bits >> l) & 1ull);
+        cx<CR> nv = mk<CR>(0, 0);
+        for (int i = 0; i < cl; ++i) {
+          cx<CR> vi;
+          vi.re = shidx(v.re, base + i);
+          vi.im = shidx(v.im, base + i);
+          if (lg < cr) {
+            cx<CR> a = ld<CR>(A + (i * 2 + b) * cr + lg);
+            if (plus) a = cadd(a, ld<CR>(A + (i * 2 + 1) * cr + lg));
+            nv = cmac(nv, vi, a);
+          }
+        }
+        v = plus ? cscale(nv, h) : nv;
+      }
+      if (on && lg == 0) B.amps[t] = cvt<T>(v);
+    }
+    __syncthreads();
+    return;
+  }
   for (int t = warp; t < nt; t += nw) {
     const bool plus = B.tplus[t];
     const unsigned long long bits = B.tbits[t];
@@ -1201,7 +1298,7 @@ __device__ void chain_targets(Blk<T, S>& B, int nt) {
 
 // ------------------------------------------------------------ the kernel
 template <class T, class S, class CR>
-__global__ void __launch_bounds__(512) iterate_kernel(const InstDesc* descs, int count, int* queue) {
+__global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int count, int* queue) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_idx;
   for (;;) {
@@ -1397,7 +1494,7 @@ __global__ void __launch_bounds__(512) iterate_kernel(const InstDesc* descs, int
 // the forward chain's marked amplitudes and <s|psi_{k-1}> for k-1 = k_lo..k_hi-1.
 // The gradients are written scaled by `scale` (dL/dP).
 template <class T, class S, class CR>
-__global__ void __launch_bounds__(512) adjoint_kernel(const InstDesc* descs, const double* rec, long long k_lo,
+__global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, const double* rec, long long k_lo,
                                                        long long k_hi, const double* phi, const double* psi,
                                                        double scale, double* gphi, double* gpsi, int project) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1984,7 +2081,7 @@ extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int
     sp = make_plan(n, M, xcap, chicap, sizeof(double), 0);
     if (sp.total > (size_t)smax) return fail(GMPS_ERR_UNSUPPORTED, "working set exceeds shared memory");
   }
-  const int threads = xcap <= 8 ? 32 : (xcap <= 16 ? 64 : (xcap <= 32 ? 128 : (xcap <= 64 ? 256 : 512)));
+  const int threads = xcap <= 8 ? 32 : (xcap <= 16 ? 64 : (xcap <= 32 ? 128 : 256));
 
   void* base = nullptr;
   cudaError_t e = noalloc_scratch_address(&base);
