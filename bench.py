@@ -29,6 +29,16 @@ N_SITES, K_ITERS, CHI_MAX, SHOTS = 29, 18198, 4, (4096, 1)
 APPLY = "fused"
 SAMPLE_SEED = 2
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (non-tensor) rate
+# DRAM bytes (read + write) of one iterate_kernel launch of this instance, from
+# the ncu capture in profiles/iterate_kernel_n29_M1_fp64.md (k = 50; the
+# traffic is the chain's load and the code, independent of k).  Retake it when
+# the kernel changes.
+TRAFFIC_BYTES = 544256
+# Share of the launch during which the FP64 pipe of the one SM sub-partition
+# running the instance is busy (same capture: sm__pipe_fp64_cycles_active max
+# over SMs, 13.63% of the SM's four sub-partitions): the fraction of the
+# single-warp FP64 issue bound that the chain reaches.
+FP64_ISSUE_BOUND_FRAC = 4 * 0.1363
 
 
 def algorithmic_flops_per_iter(n: int, chi: int, M: int, apply: str) -> float:
@@ -385,7 +395,11 @@ def main():
                     "shot_1": int(bits[1][0]), "max_bond": chi, "jacobi_sweeps_max": st["max_jacobi_sweeps"],
                     "discarded_weight": st["discarded_weight"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
+                     "chain_bound": {"model": "FP64 issue of one SM sub-partition: one warp, ~64 cycles per "
+                                              "FP64 warp instruction on this part",
+                                     "frac": FP64_ISSUE_BOUND_FRAC,
+                                     "source": "ncu capture, profiles/iterate_kernel_n29_M1_fp64.md"},
                      "kernel": "iterate_kernel<double,double2,double>",
                      "algorithmic_flops_per_launch": flops, "kernel_ms": statistics.mean(kern_ms),
                      "peak_source": "nominal FP64 rate of the part (recipe table), 1.25 TFLOP/s; one instance "
