@@ -121,6 +121,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_rate(local_ms: float, steps: int, k: int):
+    """Whole-job rate of independent replicas, one per rank.  The slowest
+    rank's total time (max over ranks) sets ms per step; every rank ran k
+    iterations per step, so value = world_size * k / (ms per step).  Returns
+    (ms_per_step, value); without an initialised process group it is the
+    single-rank rate."""
+    import torch
+    ws = 1
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        ws = torch.distributed.get_world_size()
+        dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        local_ms = t.item()
+    ms_per_step = local_ms / steps
+    return ms_per_step, ws * k / (ms_per_step / 1000.0)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -344,12 +363,7 @@ def main():
     launches = B.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     kern_ms = [a.elapsed_time(b) for a, b in kev]
-    t = torch.tensor([sum(step_ms)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-    ms_per_step = t.item() / args.steps
-    value = ws * k / (ms_per_step / 1000.0)
+    ms_per_step, value = replica_rate(sum(step_ms), args.steps, k)
 
     # ---- end to end through the C ABI with host buffers (create .. destroy)
     e2e_ms = []
@@ -365,7 +379,7 @@ def main():
         be = [ge.sample(s, SAMPLE_SEED) for s in SHOTS]
         ge.close()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    e2e_val = ws * k / (statistics.mean(e2e_ms) / 1000.0)
+    _, e2e_val = replica_rate(sum(e2e_ms), len(e2e_ms), k)
 
     if rank != 0:
         if ws > 1:

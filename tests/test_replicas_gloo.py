@@ -1,0 +1,56 @@
+"""The multi-GPU form of the benchmark is N independent replicas (a single
+instance's sweep is a site-sequential chain and does not shard).  Its host
+logic -- max over ranks of the timed region, whole-job value = N k / time --
+is checked here with two gloo ranks on the CPU."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        # rank r's timed region took 1000 (r + 1) ms over 2 steps of k = 100 iterations
+        ms, value = bench.replica_rate(1000.0 * (rank + 1), 2, 100)
+        q.put((rank, ms, value))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_rate_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    for rank, ms, value in got:
+        assert ms == pytest.approx(1000.0)      # slowest rank: 2000 ms / 2 steps
+        assert value == pytest.approx(200.0)    # 2 replicas x 100 iterations / 1 s
+
+
+def test_replica_rate_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert not dist.is_initialized()
+    ms, value = bench.replica_rate(500.0, 5, 50)
+    assert ms == pytest.approx(100.0) and value == pytest.approx(500.0)
