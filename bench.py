@@ -172,7 +172,7 @@ print(json.dumps({{"iters": done, "seconds": dt}}))
                       f"({APPLY} contraction, NumPy FP64, OMP_NUM_THREADS=1), {res['seconds']:.1f} s"}
 
 
-def extra_workloads(B, inputs, sptr, kslice_batch=100):
+def extra_workloads(B, inputs, sptr):
     """Other forms and workloads, each measured once outside the headline's
     timed region (CUDA events on the handle's stream)."""
     import numpy as np
@@ -203,22 +203,21 @@ def extra_workloads(B, inputs, sptr, kslice_batch=100):
                             "shots_4096_marked": int(np.sum(bits == inst.marked[0])),
                             "dtype": {"c64": "c64 (FP64 QR/SVD)", "dw": "f32x2 double-word"}[dt]}
         g.close()
-    # batched: 512 instances, k_i capped for a bounded measurement
+    # batched: the 512-instance workload with its full k_i = min(floor(pi/4
+    # sqrt(2^n/M)), 4000); the autotuner's timed slices (k_i capped at 10) are
+    # the warm-up, and the one timed run includes the CUDA-graph capture
     from paper_2601_03832_gb300 import autotune
     insts = inputs.config_batched(count=512)
-    for i in insts:
-        i.k = min(i.k, kslice_batch)
     thr, rec = autotune.tune_batch(insts, dtype="c64", apply=APPLY, kslice=10, stream=sptr)
     bt = B.GroverBatch(insts, dtype="c64", apply=APPLY, stream=sptr)
     bt.set_threads(thr)
-    bt.run(use_graph=True)
-    bt.result()
     sec, _ = timed(lambda: bt.run(use_graph=True))
     p, st, rc = bt.result()
     errs = [abs(p[i] - reduced.closed_form(x.n, x.M, x.k)[0]) for i, x in enumerate(insts)]
     tot = sum(x.k for x in insts)
     out["batched_512_c64"] = {"iterations_per_s": tot / sec, "seconds": sec, "total_iterations": tot,
-                              "k_cap": kslice_batch, "threads": thr, "autotune": rec, "graph": True,
+                              "k": "full, min(floor(pi/4 sqrt(2^n/M)), 4000)", "threads": thr,
+                              "autotune": rec, "graph": True,
                               "max_P_err": max(errs), "median_P_err": float(np.median(errs)),
                               "instances_with_status": int((st != 0).sum())}
     bt.close()

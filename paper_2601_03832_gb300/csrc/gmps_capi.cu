@@ -66,8 +66,9 @@ static int xcap_for(int apply, int M, int chicap) {
   return chicap + M + 1;
 }
 
+// CTA size from the expanded bond; at least two warps, so that the small
+// register-resident QR steps hand their Q formation to warp 1
 static int auto_threads(int xcap) {
-  if (xcap <= 8) return 32;
   if (xcap <= 16) return 64;
   if (xcap <= 32) return 128;
   return 256;

@@ -60,7 +60,7 @@ struct InstDesc {
 
 // Shared-memory plan of one block (bytes), identical on host and device.
 struct SmemPlan {
-  size_t off_chi, off_qb, off_soff, off_terms, off_amps, off_misc, off_qperm, off_qcn;
+  size_t off_chi, off_qb, off_soff, off_terms, off_amps, off_misc, off_qperm, off_qcn, off_tbuf;
   size_t off_rprev, off_w, off_tau, off_beta;      // QR sweep
   size_t off_mat, off_u, off_us, off_sig, off_perm;  // SVD sweep (aliases QR)
   size_t off_sites;
@@ -83,6 +83,7 @@ GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, size_t rb,
   p.off_misc = o;  o = align_up(o + 512, 16);
   p.off_qperm = o; o = align_up(o + sizeof(int) * (size_t)xcap, 16);   // QR pivots
   p.off_qcn = o;   o = align_up(o + rb * (size_t)xcap, 16);            // QR column norms
+  p.off_tbuf = o;  o = align_up(o + (cb * 32 + 16) * 2, 16);           // reflectors handed between warps
   size_t base = o;
   // QR-sweep working set
   size_t q = base;

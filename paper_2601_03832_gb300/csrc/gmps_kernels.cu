@@ -215,6 +215,7 @@ struct Blk {
   int* perm;
   int* qperm;              // QR column pivots
   T* qcn;                  // QR trailing column norms
+  unsigned char* tbuf;     // two buffers: 32 lanes' reflector registers + (p, m) of a small QR step
   int* misc;               // [0] status, [1] max sweeps, [2] sweeps sum, [3] svd count, [4] k kept
   double* dmisc;           // [0] log_norm, [1] discarded, [2..5] phase coefficients
   T* tmisc;                // [0] rank-rule eps, [1] tol, [2] discarded weight, [3..6] e^{i phi}-1 and 1-e^{i psi},
@@ -274,93 +275,19 @@ __device__ __forceinline__ int expo_abs(float x) { return ((__float_as_int(x) >>
 __device__ __forceinline__ int expo_abs(dw x) { return ((__float_as_int(x.h) >> 23) & 0xff) - 127; }
 
 // ----------------------------------------------------------- Householder QR
-// In-place QR of A (m x ncol, leading dim lda) by Householder reflectors
-// H_j = I - tau_j v_j v_j^dag with v_j = x - beta_j e_j, beta_j =
-// -e^{i arg x_j}|x|, tau_j = 1/(|x| (|x| + |x_j|)) (so that H_j x = beta_j e_j).
-// On return the strict upper triangle holds R (diagonal in beta), the
-// columns j hold v_j from row j down.
-template <class T>
-__device__ void qr_householder(cx<T>* A, int m, int ncol, int lda, T* tau, cx<T>* beta) {
-  const int p = min(m, ncol);
-  const int G = pow2_cap32(m);
-  const Grp g = make_grp(G);
-  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
-  for (int j = 0; j < p; ++j) {
-    if (threadIdx.x < G) {
-      // optional exact power-of-two scaling of the column (rows >= j)
-      int em = -2000;
-      if (K<T>::kScaleColumns) {
-        for (int i = j + threadIdx.x; i < m; i += G) {
-          const cx<T> x = A[i * lda + j];
-          if (x.re != (T)0) em = max(em, expo_abs(x.re));
-          if (x.im != (T)0) em = max(em, expo_abs(x.im));
-        }
-        for (int o = G >> 1; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(gmask, em, o));
-      }
-      const bool scl = K<T>::kScaleColumns && em > -2000;
-      const T sc = scl ? pow2<T>(-em) : (T)1;
-      T s = 0;
-      for (int i = j + threadIdx.x; i < m; i += G) {
-        cx<T> x = A[i * lda + j];
-        if (scl) {
-          x = cscale(x, sc);
-          A[i * lda + j] = x;
-        }
-        s += abs2(x);
-      }
-      for (int o = G >> 1; o > 0; o >>= 1) s += shx_m(s, o, gmask);
-      if (threadIdx.x == 0) {
-        cx<T> x0 = A[j * lda + j];
-        T a2 = abs2(x0);
-        cx<T> b = mk<T>(0, 0);
-        T t = 0;
-        if (s > K<T>::tiny2()) {
-          T inv = rsqrt(s);
-          T nrm = s * inv;
-          cx<T> ph = mk<T>(1, 0);
-          T ax0 = 0;
-          if (a2 > K<T>::phase_floor() * s) {
-            T ia = rsqrt(a2);
-            ax0 = a2 * ia;
-            ph = cscale(x0, ia);
-          }
-          b = cscale(ph, -nrm);
-          t = (T)1 / (nrm * (nrm + ax0));
-          A[j * lda + j] = csub(x0, b);
-        }
-        beta[j] = scl ? cscale(b, pow2<T>(em)) : b;  // R_jj of the unscaled column
-        tau[j] = t;
-      }
-    }
-    __syncthreads();
-    const T tj = tau[j];
-    const int ntask = ncol - j - 1;
-    for (int t0 = 0; t0 < ntask; t0 += g.ng) {
-      const int c = j + 1 + t0 + g.gid;
-      const bool act = (t0 + g.gid) < ntask;
-      cx<T> w = mk<T>(0, 0);
-      if (act)
-        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, A[i * lda + j], A[i * lda + c]);
-      w.re = gsum(w.re, G);
-      w.im = gsum(w.im, G);
-      if (act && tj != (T)0) {
-        const cx<T> tw = cscale(w, -tj);
-        for (int i = j + g.lg; i < m; i += G) A[i * lda + c] = cmac(A[i * lda + c], A[i * lda + j], tw);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Rank-revealing variant: Householder QR with column pivoting (largest
-// remaining column first) that stops once the largest remaining column norm
-// is at or below the rank rule's noise floor, max(m, n) eps times the largest
-// input column norm -- the directions left carry zero weight up to rounding
-// (for the Grover iterate they are the rounding of its two-dimensional span).  Column norms of the trailing block are recomputed
-// by the lane group that updates each column.  On return perm[c] is the
-// original index of the column now at position c; the first `rank` columns
-// hold the reflectors, the leading `rank` rows the upper-trapezoidal R of
-// the permuted matrix.  cn is scratch for ncol norms; ctl for 4 ints.
+// Householder reflectors H_j = I - tau_j v_j v_j^dag with v_j = x - beta_j e_j,
+// beta_j = -e^{i arg x_j}|x|, tau_j = 1/(|x| (|x| + |x_j|)), so that H_j x =
+// beta_j e_j.  The QR is rank-revealing: column pivoting (largest remaining
+// column first), stopped once the largest remaining column norm is at or
+// below the rank rule's noise floor, max(m, n) eps times the largest input
+// column norm -- the directions left carry zero weight up to rounding (for
+// the Grover iterate they are the rounding of its two-dimensional span).
+// Column norms of the trailing block are recomputed by the lane group that
+// updates each column.  In place on A (m x ncol, leading dim lda): on return
+// perm[c] is the original index of the column now at position c; the first
+// `rank` columns hold v_j from row j down, the leading `rank` rows the
+// upper-trapezoidal R of the permuted matrix (diagonal in beta).  cn is
+// scratch for ncol norms; ctl for 4 ints.
 template <class T>
 __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<T>* beta, int* perm, T* cn,
                                  int* ctl, T floor_rel2) {
@@ -883,6 +810,15 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
   }
   __syncthreads();
   int r = 1;
+  // site whose Q warp 1 still has to form from the hand-off buffer (-1: none)
+  int pend = -1;
+  const bool offload = blockDim.x >= 64;
+  auto flush_q = [&](int site) {
+    if (threadIdx.x >= 32 && threadIdx.x < 64) {
+      const int* meta = tbuf_meta<T>(B.tbuf, site & 1);
+      tiny_q_store<T, S>(tbuf_regs<T>(B.tbuf, site & 1)[threadIdx.x & 31], meta[1], meta[0], B.slot(site));
+    }
+  };
   PROF_T0
   for (int l = 0; l < n; ++l) {
     const int xl = xb(l), xr = xb(l + 1);
@@ -900,13 +836,31 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
                              ? expand_elem<T, S, CR>(B, l, i >> 1, i & 1, c, xl, mode, op, D, lbnd, cpsi, nt)
                              : mk<T>(0, 0);
         const T fl = (T)max(m, xr) * B.tmisc[0];
-        const int pt = tiny_qr<T, S>(w0, m, xr, fl * fl, dst, B.Rp);
+        cx<T> a;
+        const int pt = tiny_qr_factor<T>(w0, m, xr, fl * fl, B.Rp, a);
+        if (offload) {  // warp 1 forms Q during the next step
+          tbuf_regs<T>(B.tbuf, l & 1)[lane] = a;
+          if (lane == 0) {
+            tbuf_meta<T>(B.tbuf, l & 1)[0] = pt;
+            tbuf_meta<T>(B.tbuf, l & 1)[1] = m;
+          }
+        } else {
+          tiny_q_store<T, S>(a, m, pt, dst);
+        }
         if (threadIdx.x == 0) B.qb[l + 1] = pt;
+      } else if (pend >= 0) {
+        flush_q(pend);
       }
       __syncthreads();
       PROF_MARK(1);
+      pend = offload ? l : -1;
       r = B.qb[l + 1];
       continue;
+    }
+    if (pend >= 0) {  // the next step needs every thread: finish the pending Q first
+      flush_q(pend);
+      __syncthreads();
+      pend = -1;
     }
     expand_absorb<T, S, CR>(B, l, r, xl, xr, mode, op, D, lbnd, cpsi, nt);
     PROF_MARK(0);
@@ -1342,6 +1296,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
     B.perm = (int*)(smem + P.off_perm);
     B.qperm = (int*)(smem + P.off_qperm);
     B.qcn = (T*)(smem + P.off_qcn);
+    B.tbuf = smem + P.off_tbuf;
     S* gsites = (S*)d.sites;
     if (d.resident) {
       S* ssites = (S*)(smem + P.off_sites);
@@ -1522,6 +1477,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
   B.tmisc = (T*)(smem + P.off_misc + 256);
   B.qperm = (int*)(smem + P.off_qperm);
   B.qcn = (T*)(smem + P.off_qcn);
+  B.tbuf = smem + P.off_tbuf;
   B.Rp = (cx<T>*)(smem + P.off_rprev);
   B.W = (cx<T>*)(smem + P.off_w);
   B.tau = (T*)(smem + P.off_tau);
@@ -2081,7 +2037,7 @@ extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int
     sp = make_plan(n, M, xcap, chicap, sizeof(double), 0);
     if (sp.total > (size_t)smax) return fail(GMPS_ERR_UNSUPPORTED, "working set exceeds shared memory");
   }
-  const int threads = xcap <= 8 ? 32 : (xcap <= 16 ? 64 : (xcap <= 32 ? 128 : 256));
+  const int threads = xcap <= 16 ? 64 : (xcap <= 32 ? 128 : 256);
 
   void* base = nullptr;
   cudaError_t e = noalloc_scratch_address(&base);

@@ -7,8 +7,11 @@
 // whatever the number of active lanes, so the layouts below keep every lane
 // busy and the reductions pair their operands (two or four sums for the
 // price of one butterfly):
-//  * tiny_qr:       rank-revealing Householder QR of an m x n matrix, m <= 8,
-//                   n <= 4; column c on lanes 8c..8c+7, row i = lane & 7.
+//  * tiny_qr_factor / tiny_q_store: rank-revealing Householder QR of an
+//                   m x n matrix, m <= 8, n <= 4; column c on lanes 8c..8c+7,
+//                   row i = lane & 7.  With two or more warps the thin Q is
+//                   formed and stored by warp 1 one step behind, off the
+//                   sweep's critical path (R feeds the next step, Q does not).
 //  * tiny_svd_step: one SVD-sweep step, one-sided Jacobi on the rows of an
 //                   r x c matrix with the r x r rotation accumulator beside
 //                   it (r <= 4, c + r <= 8); row p on lanes 8p..8p+7, lane
@@ -98,10 +101,11 @@ __device__ __forceinline__ bool above_phase_floor<double>(double a2, double s) {
 // (compared exactly here, through FP32 images there), the factorisation stops
 // at the first step whose largest remaining squared norm is <= floor_rel2
 // times the largest input column's.  Each reflector is stored scaled by
-// sqrt(tau) (H = I - v v^dag).  Writes the thin Q (m x p, row-major) to dst
-// and R P^T (p x n, leading dim n) to Rp; returns p (the same in every lane).
-template <class T, class S>
-__device__ int tiny_qr(cx<T> w0, int m, int n, T floor_rel2, S* dst, cx<T>* Rp) {
+// sqrt(tau) (H = I - v v^dag).  Writes R P^T (p x n, leading dim n) to Rp and
+// leaves the reflectors in the lanes' `a` (column jj's lanes, rows >= jj) for
+// tiny_q_store; returns p (the same in every lane).
+template <class T>
+__device__ int tiny_qr_factor(cx<T> w0, int m, int n, T floor_rel2, cx<T>* Rp, cx<T>& a_out) {
   const int lane = threadIdx.x & 31;
   const int c = lane >> 3, i = lane & 7;
   const bool live = c < n && i < m;
@@ -207,8 +211,20 @@ __device__ int tiny_qr(cx<T> w0, int m, int n, T floor_rel2, S* dst, cx<T>* Rp) 
   const int p = rank;
   // R P^T: row i < p; the column at position c is original column pc
   if (live && i < p) Rp[i * n + pc] = c > i ? a : (c == i ? pick4(be0, be1, be2, be3, i) : zero);
-  // thin Q, column c = H_0 ... H_{p-1} e_c, in the lanes of column c; the
-  // first factor applied is H_{p-1} e_c = e_c - v conj(v_c) (no reduction)
+  a_out = a;
+  return p;
+}
+
+// The thin Q (m x p, row-major, to dst) from the reflectors that
+// tiny_qr_factor left in the lanes' `a`; any one warp can run it.  Column c =
+// H_0 ... H_{p-1} e_c is built in the lanes of column c; the
+  // first factor applied is H_{p-1} e_c = e_c - v conj(v_c) (no reduction).
+template <class T, class S>
+__device__ void tiny_q_store(cx<T> a, int m, int p, S* dst) {
+  const int lane = threadIdx.x & 31;
+  const int c = lane >> 3, i = lane & 7;
+  const cx<T> zero = mk<T>(0, 0);
+  TPROF_T0
   cx<T> q;
   {
     const cx<T> vl = shcx(a, (p - 1) * 8 + i), vc = shcx(a, (p - 1) * 8 + c);
@@ -229,7 +245,17 @@ __device__ int tiny_qr(cx<T> w0, int m, int n, T floor_rel2, S* dst, cx<T>* Rp) 
   }
   if (c < p && i < m) st(dst + i * p + c, q);
   TPROF_MARK(5);
-  return p;
+}
+
+// Hand-off of a small QR step between warps: two buffers (by site parity),
+// each the 32 lanes' reflector registers followed by (p, m).
+template <class T>
+__device__ __forceinline__ cx<T>* tbuf_regs(unsigned char* tb, int b) {
+  return (cx<T>*)(tb + b * (32 * sizeof(cx<T>) + 16));
+}
+template <class T>
+__device__ __forceinline__ int* tbuf_meta(unsigned char* tb, int b) {
+  return (int*)(tb + b * (32 * sizeof(cx<T>) + 16) + 32 * sizeof(cx<T>));
 }
 
 // One step of the SVD sweep at site l (rl <= 4, c = 2 kr, c + rl <= 8), by
