@@ -792,10 +792,43 @@ __device__ __forceinline__ void set_status(int* misc, int code) {
 
 #include "gmps_tiny.cuh"
 
-// One contraction followed by the QR sweep and the truncated SVD sweep.
+// Right environments of the product-state targets, folded site by site from
+// the right while the SVD sweep finalises the sites (warp 1): E <- A_s[:, b_s, :] E
+// (or (A_s[:,0,:] + A_s[:,1,:]) E / sqrt 2 for |+>^n).  A group of G lanes per
+// target (G a power of two covering every bond), lane lg holding E[lg]; after
+// site 0 lane 0 of each group holds <target|psi>.  Same quantity as
+// chain_targets, accumulated from the other end.
+template <class T, class S, class CR>
+__device__ __forceinline__ void env_fold(Blk<T, S>& B, int s, int nt, int G, cx<CR>& E) {
+  const int lane = threadIdx.x & 31, lg = lane & (G - 1), base = lane & ~(G - 1);
+  const int t = lane / G;
+  const bool on = t < nt;
+  const bool plus = on && B.tplus[t];
+  const unsigned long long bits = (on && !plus) ? B.tbits[t] : 0ull;
+  const int cl = B.chi[s], cr = B.chi[s + 1];
+  const int b = (int)((bits >> s) & 1ull);
+  const S* A = B.slot(s);
+  cx<CR> nv = mk<CR>(0, 0);
+  for (int j = 0; j < cr; ++j) {
+    cx<CR> ej;
+    ej.re = shidx(E.re, base + j);
+    ej.im = shidx(E.im, base + j);
+    if (lg < cl) {
+      cx<CR> a = ld<CR>(A + (lg * 2 + b) * cr + j);
+      if (plus) a = cadd(a, ld<CR>(A + (lg * 2 + 1) * cr + j));
+      nv = cmac(nv, a, ej);
+    }
+  }
+  E = plus ? cscale(nv, K<CR>::isq2()) : nv;
+}
+
+// One contraction followed by the QR sweep and the truncated SVD sweep.  With
+// env_nt > 0 (two or more warps, every bond within 16 lanes, env_nt targets
+// in one warp) warp 1 also computes <target|psi> of the result for the
+// env_nt targets in B.tbits/B.tplus, into B.amps, hidden under the SVD sweep.
 template <class T, class S, class CR>
 __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* lbnd, cx<T> cpsi,
-                           int nt) {
+                           int nt, int env_nt = 0) {
   const InstDesc& d = *B.d;
   const int n = B.n;
   // expanded bond at cut l (0 < l < n)
@@ -979,16 +1012,30 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
   int kr = 1;  // bond to the right of the current site after truncation
   const T eps_rule = B.tmisc[0];
   const T tol_rule = B.tmisc[1];
+  // target environments (warp 1): E holds E_{folded}; sites >= folded are in
+  const int envG = pow2_cap32(d.chicap);
+  const bool warp1 = threadIdx.x >= 32 && threadIdx.x < 64;
+  cx<CR> E = mk<CR>((threadIdx.x & (envG - 1)) == 0 ? (CR)1 : (CR)0, 0);
+  int folded = n;
   for (int l = n - 1; l >= 1; --l) {
     const int rl = B.qb[l], rr = B.qb[l + 1];
     const S* A = B.slot(l);
     const int c = 2 * kr;
     if (rl <= 4 && c + rl <= 8) {  // register-resident step (one warp)
-      if (threadIdx.x < 32) tiny_svd_step<T, S, CR>(B, l, rl, rr, kr);
+      if (threadIdx.x < 32)
+        tiny_svd_step<T, S, CR>(B, l, rl, rr, kr);
+      else if (env_nt > 0 && warp1 && folded == l + 2)
+        env_fold<T, S, CR>(B, l + 1, env_nt, envG, E);  // site l+1 is final
       __syncthreads();
       PROF_MARK(7);
+      if (env_nt > 0 && folded == l + 2) folded = l + 1;
       kr = B.misc[4];
       continue;
+    }
+    if (env_nt > 0 && folded == l + 2) {  // the block step needs every thread
+      if (warp1) env_fold<T, S, CR>(B, l + 1, env_nt, envG, E);
+      __syncthreads();
+      folded = l + 1;
     }
     // Mat = A (rl x 2 x rr) * US (rr x kr)  -> rl x (2 kr)
     for (int e = threadIdx.x; e < rl * c; e += blockDim.x) {
@@ -1174,6 +1221,14 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     for (int e = threadIdx.x; e < c; e += blockDim.x) st(A + e, cscale(B.Mat[e], inv));
     __syncthreads();
   }
+  if (env_nt > 0) {  // sites folded..1 are final, site 0 just renormalised
+    if (warp1) {
+      for (int s = folded - 1; s >= 0; --s) env_fold<T, S, CR>(B, s, env_nt, envG, E);
+      const int lane = threadIdx.x & 31;
+      if ((lane & (envG - 1)) == 0 && lane / envG < env_nt) B.amps[lane / envG] = cvt<T>(E);
+    }
+    __syncthreads();
+  }
 }
 
 // <target_t|psi> for product-state targets (basis strings or |+>^n), by the
@@ -1321,6 +1376,12 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
     __syncthreads();
     const int M = d.M;
     long long done = 0;
+    // fused form: <w|psi> and <s|psi> for the next iteration come out of the
+    // sweep (warp 1 folds the sites as the SVD sweep finalises them) when
+    // the block has a second warp and the M+1 targets fit it
+    const int envG = pow2_cap32(d.chicap);
+    const int env_nt = (d.apply == 2 && n >= 2 && blockDim.x >= 64 && envG <= 16 && M + 1 <= 32 / envG) ? M + 1 : 0;
+    bool amps_ready = false;
     for (long long it = 0; it < d.k; ++it) {
       if (B.misc[0] != 0) break;
       const long long pi = d.phase_offset + it;
@@ -1331,7 +1392,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
           B.tplus[t] = t == M;
         }
         __syncthreads();
-        chain_targets<T, S, CR>(B, M + 1);
+        if (!amps_ready) chain_targets<T, S, CR>(B, M + 1);
         for (int t = threadIdx.x; t <= M; t += blockDim.x) {
           d.rec[(it * (M + 1) + t) * 2] = (double)B.amps[t].re;
           d.rec[(it * (M + 1) + t) * 2 + 1] = (double)B.amps[t].im;
@@ -1395,7 +1456,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
           B.tplus[t] = t == M;
         }
         __syncthreads();
-        {
+        if (!amps_ready) {
           PROF_T0
           chain_targets<T, S, CR>(B, M + 1);
           PROF_MARK(10);
@@ -1411,7 +1472,8 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
           B.tcoef[t] = mk<T>(-c.re, -c.im);
         }
         __syncthreads();
-        sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), M + 1);
+        sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), M + 1, env_nt);
+        amps_ready = env_nt > 0;
       }
       __syncthreads();
       if (B.misc[0] == 0) ++done;
