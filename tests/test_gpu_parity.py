@@ -212,3 +212,26 @@ def test_batched_many_marked_fp64_all_instances(B):
     assert rc == 0 and not st.any()
     errs = [abs(p[i] - reduced.closed_form(x.n, x.M, x.k)[0]) for i, x in enumerate(insts)]
     assert max(errs) < TOL_P_F64, (int(np.argmax(errs)), max(errs))
+
+
+@pytest.mark.parametrize("dtype", ["c128", "dw"])
+@pytest.mark.parametrize("apply", ["mpo", "split", "fused"])
+@pytest.mark.parametrize("n,M", [(12, 1), (10, 2)])
+def test_cta_sizes_agree_with_oracle(B, apply, n, M, dtype):
+    """One warp (every small step inline), two warps (Q formed by warp 1,
+    target environments folded during the SVD sweep) and eight warps run the
+    same iteration: each against the dense oracle, with general phases."""
+    marked = inputs.marked_strings(n, M, seed=500 + n + M)
+    rng = np.random.default_rng(17 * n + M)
+    k = 9
+    phis, psis = rng.normal(np.pi, 0.5, k), rng.normal(np.pi, 0.5, k)
+    ref = sv.grover(n, marked, k, phis, psis)
+    for threads in (32, 64, 256):
+        g = B.GroverMPS(n, marked, dtype=dtype, apply=apply, chi_max=16, threads=threads)
+        g.iterate(k, phis, psis)
+        v = dense_from_sites(g.export())
+        assert np.abs(v - ref).max() < TOL[dtype][1], threads
+        st = g.stats()
+        for cut in range(1, n):
+            assert st["chi"][cut] == reduced.exact_bond(n, marked, k, cut, phis, psis), (threads, cut)
+        g.close()
