@@ -33,12 +33,13 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (non-tensor) rate
 # the ncu capture in profiles/iterate_kernel_n29_M1_fp64.md (k = 50; the
 # traffic is the chain's load and the code, independent of k).  Retake it when
 # the kernel changes.
-TRAFFIC_BYTES = 544256
-# Share of the launch during which the FP64 pipe of the one SM sub-partition
-# running the instance is busy (same capture: sm__pipe_fp64_cycles_active max
-# over SMs, 13.63% of the SM's four sub-partitions): the fraction of the
-# single-warp FP64 issue bound that the chain reaches.
-FP64_ISSUE_BOUND_FRAC = 4 * 0.1363
+TRAFFIC_BYTES = 210176
+# FP64 pipe busy time of the SM running the instance, summed over its four
+# sub-partitions, as a share of the launch (same capture:
+# sm__pipe_fp64_cycles_active max over SMs, 15.16% of the SM's four pipes):
+# the instance's FP64 instructions issued back to back on one pipe would take
+# this share of the launch -- the FP64 issue bound of the dependent chain.
+FP64_ISSUE_BOUND_FRAC = 4 * 0.1516
 
 
 def algorithmic_flops_per_iter(n: int, chi: int, M: int, apply: str) -> float:
@@ -409,8 +410,9 @@ def main():
                     "discarded_weight": st["discarded_weight"]},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
-                     "chain_bound": {"model": "FP64 issue of one SM sub-partition: one warp, ~64 cycles per "
-                                              "FP64 warp instruction on this part",
+                     "chain_bound": {"model": "FP64 issue bound: the instance's FP64 warp instructions (~64 "
+                                              "cycles each on this part, two warps on two SM sub-partitions) "
+                                              "back to back on one pipe, as a share of the launch",
                                      "frac": FP64_ISSUE_BOUND_FRAC,
                                      "source": "ncu capture, profiles/iterate_kernel_n29_M1_fp64.md"},
                      "kernel": "iterate_kernel<double,double2,double>",
