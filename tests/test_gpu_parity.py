@@ -235,3 +235,22 @@ def test_cta_sizes_agree_with_oracle(B, apply, n, M, dtype):
         for cut in range(1, n):
             assert st["chi"][cut] == reduced.exact_bond(n, marked, k, cut, phis, psis), (threads, cut)
         g.close()
+
+
+def test_paper_experiments_small_n(B):
+    """The paper's sweeps (M = 1, k = round(pi/4 sqrt N)) on the built path at
+    small n: FP64 marked probability against the closed form, complex64
+    within its stated bound, shot counts within 6 sigma of the binomial mean."""
+    from paper_2601_03832_gb300 import experiments as ex
+    ns = [4, 7, 10]
+    for r in ex.precision_sweep(ns):
+        Pc = reduced.closed_form(r["n"], 1, r["k"])[0]
+        assert abs(r["c128"]["P_marked"] - Pc) < TOL_P_F64
+        assert abs(r["c64"]["P_marked"] - Pc) < TOL_P_C64
+        assert r["c128"]["max_bond"] <= 2
+    for r in ex.shot_sweep([2, 5, 9]):
+        Pc = reduced.closed_form(r["n"], 1, r["k"])[0]
+        for s, cnt in r["marked_counts"].items():
+            s = int(s)
+            assert 0 <= cnt <= s
+            assert abs(cnt - s * Pc) <= 6 * math.sqrt(s * Pc * (1 - Pc)) + 1

@@ -304,3 +304,11 @@ def test_golden_file_is_current():
     assert abs(e["P"] - 0.99994534610911) < 1e-13
     assert abs(g["n29_M1_k18198"]["P"] - 0.99999999848124) < 1e-13
     assert abs(g["n40_M32_k1000"]["P"] - 1.1652723977320e-4) < 1e-15
+
+
+def test_paper_iteration_count_rule():
+    """Eq. 8, k = round(pi/4 sqrt N): 50 at n = 12, 18198 at n = 29, and 9 at
+    n = 7 (where floor would give 8)."""
+    from paper_2601_03832_gb300.experiments import k_paper
+    assert k_paper(12) == 50 and k_paper(29) == 18198 and k_paper(7) == 9
+    assert [k_paper(n) for n in (2, 3, 4, 5)] == [2, 2, 3, 4]
