@@ -11,11 +11,14 @@
 // the block's threads parallelise inside each small factorisation: lane
 // groups own matrix columns (QR) or row pairs (Jacobi) and reduce with warp
 // shuffles; all working matrices live in shared memory and, for small
-// instances, the whole chain does too.
+// instances, the whole chain does too.  Steps small enough for one warp run
+// in registers instead (gmps_tiny.cuh), and a second warp then takes the
+// work off the sweep's critical path (Q formation, target environments).
 //
 // Arithmetic forms (template parameters): T = real type of the QR/SVD and
-// scalar bookkeeping (double), S = storage type of a complex site element
-// (double2 or float2), CR = real type of the contractions (double or float).
+// scalar bookkeeping (double, or the double-word dw), S = storage type of a
+// complex site element (double2, float2 or dw2), CR = real type of the
+// contractions (double, float or dw).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
