@@ -98,3 +98,28 @@ def test_backward_requires_differentiable_handle(B):
     with pytest.raises(B.GMPSError) as e:
         g.backward(-1.0)
     assert e.value.status == 7
+
+
+def test_concurrent_batch_matches_one_by_one(B):
+    """loss_and_grad_batch runs the phase vectors side by side (one handle,
+    stream and host thread each); every vector's loss and gradients equal
+    those of the same handle run alone, and the reduced model's."""
+    import torch
+    from paper_2601_03832_gb300 import autograd as AG
+    n, M, K = 12, 3, 16
+    marked = inputs.marked_strings(n, M, seed=91)
+    rng = np.random.default_rng(5)
+    phis, psis = rng.normal(np.pi, 0.3, (6, K)), rng.normal(np.pi, 0.3, (6, K))
+    L, gphi, gpsi = AG.loss_and_grad_batch(n, marked, phis, psis)
+    torch.cuda.synchronize()
+    for b in range(len(phis)):
+        h = AG.differentiable_handle(n, marked, K)
+        h.iterate(K, phis[b], psis[b])
+        l1 = 1.0 - h.prob_marked()
+        g1, g2 = h.backward(-1.0)
+        h.close()
+        assert abs(L[b] - l1) < 1e-14
+        assert np.abs(gphi[b] - g1).max() < 1e-14 and np.abs(gpsi[b] - g2).max() < 1e-14
+        Lr, rphi, rpsi = reduced.loss_and_grad(n, M, phis[b], psis[b])
+        assert abs(L[b] - Lr) < 1e-10
+        assert np.abs(gphi[b] - rphi).max() < TOL_G and np.abs(gpsi[b] - rpsi).max() < TOL_G
