@@ -37,7 +37,7 @@ class GroverPhases(torch.autograd.Function):
                 torch.from_numpy(np.ascontiguousarray(gpsi)).to(v2, d2), None)
 
 
-def differentiable_handle(n, marked, K, dtype="c128", apply="split", chi_max=None, checkpoint_every=8,
+def differentiable_handle(n, marked, K, dtype="c128", apply="fused", chi_max=None, checkpoint_every=8,
                           stream=None):
     """A handle able to record K iterations for GroverPhases."""
     return binding.GroverMPS(n, marked, dtype=dtype, apply=apply,
@@ -46,7 +46,7 @@ def differentiable_handle(n, marked, K, dtype="c128", apply="split", chi_max=Non
                              stream=stream)
 
 
-def loss_and_grad_batch(n, marked, phis, psis, dtype="c128", apply="split", chi_max=None, checkpoint_every=8):
+def loss_and_grad_batch(n, marked, phis, psis, dtype="c128", apply="fused", chi_max=None, checkpoint_every=8):
     """L = 1 - P_marked and its gradients for B independent phase vectors
     (rows of phis, psis: B x K), all at once.  Each vector gets its own
     handle and CUDA stream and is driven from its own host thread (the C

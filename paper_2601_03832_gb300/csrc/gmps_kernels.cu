@@ -1502,6 +1502,77 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
 }
 
 // ------------------------------------------------------------------ adjoint
+// One costate step as two direct sums (D(-psi_k) with the |s> term, then
+// O(-phi_k) with the marked terms), for arenas sized for the split form;
+// gradients as in adjoint_kernel.  Leaves the targets' table set to the M
+// marked strings.
+template <class T, class S, class CR>
+__device__ void adjoint_two_steps(Blk<T, S>& B, const double* rec, long long k, long long k_lo, const double* phi,
+                                  const double* psi, double scale, double* gphi, double* gpsi) {
+  const InstDesc& d = *B.d;
+  const int M = d.M;
+  if (threadIdx.x == 0) {
+    double sp, cp, ss, cs;
+    sincos(phi[k - 1], &sp, &cp);
+    sincos(psi[k - 1], &ss, &cs);
+    B.dmisc[2] = cp;
+    B.dmisc[3] = sp;
+    B.dmisc[4] = cs;
+    B.dmisc[5] = ss;
+    B.tbits[0] = 0ull;
+    B.tplus[0] = 1;
+  }
+  __syncthreads();
+  const double cp = B.dmisc[2], sp = B.dmisc[3], cs = B.dmisc[4], ss = B.dmisc[5];
+  // <s|mu_k> of the normalised chain, scale lambda = e^{log norm}
+  chain_targets<T, S, CR>(B, 1);
+  double smr = 0, smi = 0;  // <s|mu_k> (thread 0)
+  if (threadIdx.x == 0) {
+    const double lam = exp(B.dmisc[0]);
+    smr = lam * (double)B.amps[0].re;
+    smi = lam * (double)B.amps[0].im;
+    // nu = D(-psi) mu = (1 - e^{-i psi}) <s|mu> |s> - mu
+    const cx<T> c1 = mk<T>((T)(1.0 - cs), (T)ss);
+    B.tcoef[0] = cmul(c1, B.amps[0]);
+  }
+  __syncthreads();
+  sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), 1);
+  if (B.misc[0] != 0) return;
+  for (int t = threadIdx.x; t < M; t += blockDim.x) {
+    B.tbits[t] = d.marked[t];
+    B.tplus[t] = 0;
+  }
+  __syncthreads();
+  chain_targets<T, S, CR>(B, M);
+  if (threadIdx.x == 0) {
+    const double lam = exp(B.dmisc[0]);
+    const double* S_ = rec + (k - 1 - k_lo) * (M + 1) * 2;
+    double zr = 0, zi = 0, sr = 0, si = 0;  // sum conj(nu) psi, sum psi
+    for (int t = 0; t < M; ++t) {
+      const double nr = (double)B.amps[t].re, ni = (double)B.amps[t].im;
+      const double pr = S_[2 * t], pim = S_[2 * t + 1];
+      zr += nr * pr + ni * pim;
+      zi += nr * pim - ni * pr;
+      sr += pr;
+      si += pim;
+    }
+    zr *= lam;
+    zi *= lam;
+    gphi[k - 1] = scale * (-2.0 * (sp * zr + cp * zi));
+    const double h = d.inv_sqrt_N;
+    const double er = cp - 1.0, ei = sp;
+    const double sor = S_[2 * M] + h * (er * sr - ei * si);
+    const double soi = S_[2 * M + 1] + h * (er * si + ei * sr);
+    const double qr = smr * sor + smi * soi, qi = smr * soi - smi * sor;
+    gpsi[k - 1] = scale * (2.0 * (ss * qr + cs * qi));
+    // mu_{k-1} = O(-phi) nu = nu + (e^{-i phi} - 1) sum_w nu(w)|w>
+    const cx<T> c2 = mk<T>((T)(cp - 1.0), (T)(-sp));
+    for (int t = 0; t < M; ++t) B.tcoef[t] = cmul(c2, B.amps[t]);
+  }
+  __syncthreads();
+  sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(1, 0), M);
+}
+
 // Reverse sweep of the phase gradient of P = sum_w |<w|psi_K>|^2 over
 // iterations k_hi..k_lo+1 (1-based), on the costate chain of `descs[0]`:
 //   mu_K = Pi_W psi_K  (project != 0: built from the chain itself),
@@ -1509,8 +1580,12 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
 //   dP/dphi_k = 2 Re[ i e^{i phi_k} sum_w conj(nu_k(w)) psi_{k-1}(w) ],
 //   dP/dpsi_k = 2 Re[ -i e^{i psi_k} conj(<s|mu_k>) <s|O_k psi_{k-1}> ],
 //   <s|O_k psi> = <s|psi> + (e^{i phi_k} - 1) 2^{-n/2} sum_w psi(w).
-// Each costate step is a direct-sum contraction followed by the QR and SVD
-// sweeps; the costate's norm is carried by the chain's log-norm.  rec holds
+// Each costate step applies G_k^dag = O(-phi_k) D(-psi_k) as one direct sum
+// (mu_{k-1} = -mu_k + (1 - e^{-i psi_k}) <s|mu_k> |s> + (e^{-i phi_k} - 1)
+// sum_w nu_k(w) |w>, with nu_k(w) = (1 - e^{-i psi_k}) <s|mu_k> 2^{-n/2} -
+// mu_k(w)) followed by the QR and SVD sweeps (two direct sums, D then O, when
+// the arena is sized for the split form); the costate's norm is carried by
+// the chain's log-norm.  rec holds
 // the forward chain's marked amplitudes and <s|psi_{k-1}> for k-1 = k_lo..k_hi-1.
 // The gradients are written scaled by `scale` (dL/dP).
 template <class T, class S, class CR>
@@ -1562,7 +1637,6 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
   }
   DevStats* ds = d.stats;
   for (int l = threadIdx.x; l <= n; l += blockDim.x) B.chi[l] = ds->chi[l];
-  __shared__ double s_g[4];
   if (threadIdx.x == 0) {
     B.misc[0] = ds->status;
     B.misc[1] = ds->max_jacobi_sweeps;
@@ -1575,82 +1649,79 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
     B.tmisc[2] = (T)0;
   }
   __syncthreads();
+  // targets: the marked strings (t < M) and |s> = |+>^n (t = M)
+  for (int t = threadIdx.x; t <= M; t += blockDim.x) {
+    B.tbits[t] = t < M ? d.marked[t] : 0ull;
+    B.tplus[t] = t == M;
+  }
+  __syncthreads();
+  // with a second warp the targets' amplitudes of each new costate come out
+  // of its sweep (environments folded as the SVD sweep finalises the sites)
+  // G_k^dag as one direct sum needs the expanded bond chi + M + 1 (the
+  // fused and MPO arenas have it; a split-form arena gets the two steps)
+  const bool fused = d.xcap >= d.chicap + M + 1;
+  const int envG = pow2_cap32(d.chicap);
+  const int env_nt =
+      (fused && n >= 2 && blockDim.x >= 64 && envG <= 16 && M + 1 <= 32 / envG) ? M + 1 : 0;
+  bool amps_ready = false;
   if (project) {
     // mu_K = sum_w psi_K(w) |w>: a direct sum without the chain's own block
-    for (int t = threadIdx.x; t < M; t += blockDim.x) {
-      B.tbits[t] = d.marked[t];
-      B.tplus[t] = 0;
-    }
-    __syncthreads();
     chain_targets<T, S, CR>(B, M);
     for (int t = threadIdx.x; t < M; t += blockDim.x) B.tcoef[t] = B.amps[t];
     __syncthreads();
-    sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(0, 0), M);
+    sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(0, 0), M, env_nt);
+    amps_ready = env_nt > 0;
   }
   for (long long k = k_hi; k > k_lo && B.misc[0] == 0; --k) {
+    if (!fused) {
+      adjoint_two_steps<T, S, CR>(B, rec, k, k_lo, phi, psi, scale, gphi, gpsi);
+      continue;
+    }
+    // <w|mu_k> and <s|mu_k> of the normalised chain (scale lambda = e^{log norm})
+    if (!amps_ready) chain_targets<T, S, CR>(B, M + 1);
     if (threadIdx.x == 0) {
       double sp, cp, ss, cs;
       sincos(phi[k - 1], &sp, &cp);
       sincos(psi[k - 1], &ss, &cs);
-      B.dmisc[2] = cp;
-      B.dmisc[3] = sp;
-      B.dmisc[4] = cs;
-      B.dmisc[5] = ss;
-      B.tbits[0] = 0ull;
-      B.tplus[0] = 1;
-    }
-    __syncthreads();
-    const double cp = B.dmisc[2], sp = B.dmisc[3], cs = B.dmisc[4], ss = B.dmisc[5];
-    // <s|mu_k> of the normalised chain, scale lambda_mu = e^{log norm}
-    chain_targets<T, S, CR>(B, 1);
-    if (threadIdx.x == 0) {
       const double lam = exp(B.dmisc[0]);
-      s_g[0] = lam * (double)B.amps[0].re;
-      s_g[1] = lam * (double)B.amps[0].im;
-      // nu = D(-psi) mu = (1 - e^{-i psi}) <s|mu> |s> - mu
+      const double h = d.inv_sqrt_N;
+      // nu = D(-psi) mu = (1 - e^{-i psi}) <s|mu> |s> - mu, so that
+      // nu(w) = (1 - e^{-i psi}) <s|mu> 2^{-n/2} - mu(w)
       const cx<T> c1 = mk<T>((T)(1.0 - cs), (T)ss);
-      B.tcoef[0] = cmul(c1, B.amps[0]);
-    }
-    __syncthreads();
-    sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), 1);
-    if (B.misc[0] != 0) break;
-    for (int t = threadIdx.x; t < M; t += blockDim.x) {
-      B.tbits[t] = d.marked[t];
-      B.tplus[t] = 0;
-    }
-    __syncthreads();
-    chain_targets<T, S, CR>(B, M);
-    if (threadIdx.x == 0) {
-      const double lam = exp(B.dmisc[0]);
+      const cx<T> cs_mu = cmul(c1, B.amps[M]);
+      // mu_{k-1} = O(-phi) nu = (1 - e^{-i psi}) <s|mu> |s> - mu + (e^{-i phi} - 1) sum_w nu(w) |w>
+      const cx<T> c2 = mk<T>((T)(cp - 1.0), (T)(-sp));
       const double* S_ = rec + (k - 1 - k_lo) * (M + 1) * 2;
       double zr = 0, zi = 0, sr = 0, si = 0;  // sum conj(nu) psi, sum psi
       for (int t = 0; t < M; ++t) {
-        const double nr = (double)B.amps[t].re, ni = (double)B.amps[t].im;
+        const cx<T> nu = csub(cscale(cs_mu, (T)h), B.amps[t]);
+        const double nr = (double)nu.re, ni = (double)nu.im;
         const double pr = S_[2 * t], pim = S_[2 * t + 1];
         zr += nr * pr + ni * pim;
         zi += nr * pim - ni * pr;
         sr += pr;
         si += pim;
+        B.tcoef[t] = cmul(c2, nu);
       }
+      B.tcoef[M] = cs_mu;
       zr *= lam;
       zi *= lam;
       // dP/dphi = 2 Re[i e^{i phi} z] = -2 (sin(phi) zr + cos(phi) zi)
       gphi[k - 1] = scale * (-2.0 * (sp * zr + cp * zi));
       // <s|O psi> = <s|psi> + (e^{i phi} - 1) 2^{-n/2} sum_w psi(w)
-      const double h = d.inv_sqrt_N;
       const double er = cp - 1.0, ei = sp;
       const double sor = S_[2 * M] + h * (er * sr - ei * si);
       const double soi = S_[2 * M + 1] + h * (er * si + ei * sr);
-      // q = conj(<s|mu>) <s|O psi>
-      const double qr = s_g[0] * sor + s_g[1] * soi, qi = s_g[0] * soi - s_g[1] * sor;
+      // q = conj(<s|mu>) <s|O psi>, <s|mu> = lambda <s|mu>_normalised
+      const double smr = lam * (double)B.amps[M].re, smi = lam * (double)B.amps[M].im;
+      const double qr = smr * sor + smi * soi, qi = smr * soi - smi * sor;
       // dP/dpsi = 2 Re[-i e^{i psi} q] = 2 (sin(psi) qr + cos(psi) qi)
       gpsi[k - 1] = scale * (2.0 * (ss * qr + cs * qi));
-      // mu_{k-1} = O(-phi) nu = nu + (e^{-i phi} - 1) sum_w nu(w)|w>
-      const cx<T> c2 = mk<T>((T)(cp - 1.0), (T)(-sp));
-      for (int t = 0; t < M; ++t) B.tcoef[t] = cmul(c2, B.amps[t]);
     }
     __syncthreads();
-    sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(1, 0), M);
+    // G_k^dag mu as one direct sum: -mu plus M + 1 product states
+    sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), M + 1, env_nt);
+    amps_ready = env_nt > 0;
   }
   __syncthreads();
   if (d.resident) {
