@@ -71,7 +71,8 @@ def loss_and_grad_batch(n, marked, phis, psis, dtype="c128", apply="fused", chi_
         return 1.0 - p, gphi, gpsi
 
     try:
-        with ThreadPoolExecutor(max_workers=nb) as ex:
+        # more concurrent single-block launches than SMs buy nothing
+        with ThreadPoolExecutor(max_workers=min(nb, 152)) as ex:
             out = list(ex.map(run, range(nb)))
     finally:
         for h in handles:
