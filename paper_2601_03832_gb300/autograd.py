@@ -72,7 +72,8 @@ def loss_and_grad_batch(n, marked, phis, psis, dtype="c128", apply="fused", chi_
 
     try:
         # more concurrent single-block launches than SMs buy nothing
-        with ThreadPoolExecutor(max_workers=min(nb, 152)) as ex:
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        with ThreadPoolExecutor(max_workers=max(1, min(nb, sms))) as ex:
             out = list(ex.map(run, range(nb)))
     finally:
         for h in handles:
