@@ -530,7 +530,8 @@ __device__ __forceinline__ bool nn_eq<double>(double a, double b) {
 // from exact power-of-two-scaled images of the T-precision entries, then
 // normalised in T.  Returns false when the pair is left alone (a row below the
 // noise floor skip2, the pair orthogonal to tolf, or a degenerate angle); else
-// cc = cos and (sre, sim) = sin * g/|g|, with cc^2 + |s|^2 = 1 to T's rounding.
+// cc = cos and (sre, sim) = sin * g/|g|, with cc^2 + |s|^2 = 1 to T's rounding
+// (normalised through rho = c^2 + |s|^2, or for small angles through c).
 // The angle is kept to IEEE FP32 accuracy (not MUFU estimates): a sloppier
 // angle costs extra rotations, whose rounding lifts the noise rows of
 // rank-deficient matrices toward the rank rule's threshold.
@@ -550,9 +551,15 @@ __device__ __forceinline__ bool jacobi_rotation(T a, T b, cx<T> gg, float tolf, 
   if (!(tt != 0.f && isfinite(tt))) return false;
   const float cf = rsqrtf(fmaf(tt, tt, 1.f));
   const float sf = cf * tt;
-  cc = widen<T>(cf);
   sre = widen<T>(sf * (gr / gabs));
   sim = widen<T>(sf * (gi / gabs));
+  if (fabsf(tt) < 3.0517578e-05f) {
+    // small angle (|t| < 2^-15): keep s as rounded and take c = 1 - |s|^2/2,
+    // so c^2 + |s|^2 = 1 + |s|^4/4 = 1 to T's rounding (|s|^4 < 2^-60)
+    cc = fma(fma(sre, sre, sim * sim), (T)-0.5f, (T)1);
+    return true;
+  }
+  cc = widen<T>(cf);
   const T rho = fma(cc, cc, fma(sre, sre, sim * sim));
   const T dd = rho - (T)1;
   const T f = fma(dd, fma(dd, (T)0.375f, (T)-0.5f), (T)1);

@@ -296,8 +296,11 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
   const T fl = (T)max(rl, c) * eps_rule * (T)0.25f;
   const T skip2 = frob * fl * fl;
   TPROF_MARK(6);
-  // Jacobi sweeps; the round-robin rounds pair row p with p ^ dx
+  // Jacobi sweeps; the round-robin rounds pair row p with p ^ dx.  own2 keeps
+  // this row's |x_p|^2 from the latest round (sigma_p^2 once a sweep ends
+  // without rotating)
   int sw = 0;
+  T own2 = 0;
   if (rl >= 2) {
     sw = -1;
     const int nround = rl == 2 ? 1 : 3;
@@ -321,6 +324,7 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
           a = shidx(s8, 0);
           b = shidx(s8, 8);
           gg = mk<T>(shidx(s8, 16), shidx(s8, 24));
+          own2 = p == 0 ? a : b;
         } else {
           const cx<T> xp = isP ? x : y, xq = isP ? y : x;
           const cx<T> xm = j < c ? x : zero;
@@ -329,6 +333,7 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
           a = shidx(r4, lp);
           b = shidx(r4, lq);
           gg = mk<T>(shidx(r4, lp + 2), shidx(r4, lp + 4));
+          own2 = isP ? a : b;
         }
         T cc, sre, sim;
         const bool rot = p < rl && q < rl && jacobi_rotation<T>(a, b, gg, K<T>::jtolf(), skip2, cc, sre, sim);
@@ -346,8 +351,9 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
     }
   }
   TPROF_MARK(8);
-  // sigma_p^2 (rows are orthogonal), ranks, rank rule
-  const T sp = sum8(inM ? abs2(x) : (T)0);
+  // sigma_p^2 (rows are orthogonal): the last sweep's Gram diagonal when it
+  // rotated nothing, else summed afresh; ranks, rank rule
+  const T sp = sw > 0 ? (row ? own2 : (T)0) : sum8(inM ? abs2(x) : (T)0);
   const T s0 = shidx(sp, 0), s1 = shidx(sp, 8), s2 = shidx(sp, 16), s3 = shidx(sp, 24);
   int rk[4];
 #pragma unroll
