@@ -33,13 +33,13 @@ FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (non-tensor) rate
 # the ncu capture in profiles/iterate_kernel_n29_M1_fp64.md (k = 50; the
 # traffic is the chain's load and the code, independent of k).  Retake it when
 # the kernel changes.
-TRAFFIC_BYTES = 210176
+TRAFFIC_BYTES = 210432
 # FP64 pipe busy time of the SM running the instance, summed over its four
 # sub-partitions, as a share of the launch (same capture:
-# sm__pipe_fp64_cycles_active max over SMs, 15.16% of the SM's four pipes):
+# sm__pipe_fp64_cycles_active max over SMs, 14.72% of the SM's four pipes):
 # the instance's FP64 instructions issued back to back on one pipe would take
 # this share of the launch -- the FP64 issue bound of the dependent chain.
-FP64_ISSUE_BOUND_FRAC = 4 * 0.1516
+FP64_ISSUE_BOUND_FRAC = 4 * 0.1472
 
 
 def algorithmic_flops_per_iter(n: int, chi: int, M: int, apply: str) -> float:
