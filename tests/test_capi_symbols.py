@@ -36,3 +36,35 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
         assert "not built" in str(e)
     else:
         raise AssertionError("load() must raise when the CUDA library is missing")
+
+
+def test_config_validation_needs_no_gpu():
+    """grover_mps_create_ex checks its configuration on the host before any
+    CUDA call: each invalid field is refused with its status and a message."""
+    import pytest
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_03832_gb300 import binding as B
+    cases = [
+        (dict(n=0, marked=[0]), 1, "n must be"),
+        (dict(n=65, marked=[0]), 1, "n must be"),
+        (dict(n=5, marked=[]), 1, "M must be >= 1"),
+        (dict(n=2, marked=[0, 1, 2, 3]), 1, "M must be < 2^n"),
+        (dict(n=20, marked=list(range(65))), 9, "built maximum"),
+        (dict(n=5, marked=[3, 3]), 1, "duplicate"),
+        (dict(n=5, marked=[40]), 1, "bits >= n"),
+        (dict(n=5, marked=[3], chi_max=0), 1, "chi_max"),
+        (dict(n=5, marked=[3], tol=-1.0), 1, "tol"),
+        (dict(n=5, marked=[3], tol=float("nan")), 1, "tol"),
+        (dict(n=5, marked=[3], dtype=7), 1, "dtype"),
+        (dict(n=5, marked=[3], apply=3), 1, "apply"),
+        (dict(n=5, marked=[3], threads=48), 1, "threads"),
+        (dict(n=5, marked=[3], threads=512), 1, "threads"),
+        (dict(n=5, marked=[3], max_sweeps=-1), 1, "max_sweeps"),
+    ]
+    for kw, status, text in cases:
+        n, marked = kw.pop("n"), kw.pop("marked")
+        with pytest.raises(B.GMPSError) as e:
+            B.GroverMPS(n, marked, **kw)
+        assert e.value.status == status, (n, marked, kw)
+        assert text in str(e.value), (str(e.value), text)
