@@ -54,3 +54,15 @@ def test_replica_rate_single_process():
     assert not dist.is_initialized()
     ms, value = bench.replica_rate(500.0, 5, 50)
     assert ms == pytest.approx(100.0) and value == pytest.approx(500.0)
+
+
+def test_flop_model_matches_the_stated_counts():
+    """The roofline's algorithmic flops per iteration (Householder QR + thin Q
+    2*4(2mn^2 - 2n^3/3), thin SVD 4(14mn^2 + 8n^3), 8 flops per complex MAC)
+    at the n = 12 and n = 29 workloads: ~1.8e5 (MPO form) and ~8.6e4 (direct
+    sum) at n = 12, 2.27e5 for the fused n = 29 headline."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.algorithmic_flops_per_iter(12, 2, 1, "mpo") == pytest.approx(1.8e5, rel=0.02)
+    assert bench.algorithmic_flops_per_iter(12, 2, 1, "fused") == pytest.approx(8.6e4, rel=0.05)
+    assert bench.algorithmic_flops_per_iter(29, 2, 1, "fused") == pytest.approx(2.27e5, rel=0.01)
