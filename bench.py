@@ -28,31 +28,26 @@ sys.path.insert(0, ROOT)
 N_SITES, K_ITERS, CHI_MAX, SHOTS = 29, 18198, 4, (4096, 1)
 APPLY = "fused"
 SAMPLE_SEED = 2
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 (non-tensor) rate
-# DRAM bytes (read + write) of one iterate_kernel launch of this instance, from
-# the ncu capture in profiles/iterate_kernel_n29_M1_fp64.md (k = 50; the
-# traffic is the chain's load and the code, independent of k).  Retake it when
-# the kernel changes.
-TRAFFIC_BYTES = 210432
-# FP64 pipe busy time of the SM running the instance, summed over its four
-# sub-partitions, as a share of the launch (same capture:
-# sm__pipe_fp64_cycles_active max over SMs, 14.72% of the SM's four pipes):
-# the instance's FP64 instructions issued back to back on one pipe would take
-# this share of the launch -- the FP64 issue bound of the dependent chain.
-FP64_ISSUE_BOUND_FRAC = 4 * 0.1472
+# Counters of the iterate kernel on this instance from one ncu capture (k = 50;
+# the DRAM traffic is the chain's load and store and the code, independent of
+# k): DRAM bytes (read + write) per launch, and the FP64 pipe busy share of the
+# SM running the instance (sm__pipe_fp64_cycles_active, summed over its four
+# sub-partitions).  None until a capture of the current kernel is recorded.
+CAPTURE = {"traffic_bytes": None, "fp64_pipe_share": None}
 
 
-def algorithmic_flops_per_iter(n: int, chi: int, M: int, apply: str) -> float:
-    """Real flops of one iteration at bond chi (complex = 4x real counts).
+def flops_per_iter_parts(n: int, chi: int, M: int, apply: str):
+    """Algorithmic real flops of one iteration at bond chi (complex = 4x the
+    real counts), split into (QR + SVD, contractions).
 
     Per operator contraction + sweep pair with expanded bond X:
-      contraction  R (r x X) . B_l: 2 r X chi complex MACs (8 flops each)
+      contraction  R (r x X) . B_l: 2 r X chi complex MACs (8 flops each),
+                   plus the absorption of U S into the left neighbour, 2 r chi chi
       Householder QR of the (2r) x X matrix and its thin Q:
                    2 * 4 (2 m n^2 - 2 n^3 / 3), m = 2r, n = X
       SVD of the r x 2 chi matrix (Golub & Van Loan thin-SVD count):
                    4 (14 m n^2 + 8 n^3), m = max, n = min
-      absorption of U S into the left neighbour: 2 r chi chi complex MACs
-    summed over the n sites; interior bonds r = X (after the QR sweep).
+    summed over the n - 1 site steps; interior bonds r = X (after the QR sweep).
     """
     if apply == "fused":
         ops = [chi + M + 1]
@@ -60,16 +55,31 @@ def algorithmic_flops_per_iter(n: int, chi: int, M: int, apply: str) -> float:
         ops = [chi + M, chi + 1]
     else:
         ops = [(M + 1) * chi, 2 * chi]
-    total = 0.0
+    linalg = contr = 0.0
     for X in ops:
         r = X
         m_, n_ = 2 * r, X
         qr = 2 * 4 * (2 * m_ * n_ ** 2 - 2 * n_ ** 3 / 3)
         a, b = max(r, 2 * chi), min(r, 2 * chi)
         svd = 4 * (14 * a * b ** 2 + 8 * b ** 3)
-        contr = 8 * (2 * r * X * chi) + 8 * (2 * r * chi * chi)
-        total += (n - 1) * (qr + svd + contr)
-    return total
+        linalg += (n - 1) * (qr + svd)
+        contr += (n - 1) * (8 * (2 * r * X * chi) + 8 * (2 * r * chi * chi))
+    return linalg, contr
+
+
+def algorithmic_flops_per_iter(n: int, chi: int, M: int, apply: str) -> float:
+    """Total algorithmic real flops of one iteration (flops_per_iter_parts summed)."""
+    a, b = flops_per_iter_parts(n, chi, M, apply)
+    return a + b
+
+
+def roofline_alu(flops: float, seconds: float, peak_tflops: float, peak_name: str, sms_used: int, sms: int):
+    """ALU roofline entry: achieved algorithmic TFLOP/s against the measured
+    chip peak, and against the share of it that the SMs the work ran on hold."""
+    ach = flops / seconds / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
+            "peak_source": f"measured {peak_name} (libgmps_peaks.so, this run)",
+            "sms_used": sms_used, "frac_of_sms_used": ach / (peak_tflops * sms_used / sms)}
 
 
 class ClockSampler:
@@ -173,15 +183,18 @@ print(json.dumps({{"iters": done, "seconds": dt}}))
                       f"({APPLY} contraction, NumPy FP64, OMP_NUM_THREADS=1), {res['seconds']:.1f} s"}
 
 
-def extra_workloads(B, inputs, sptr):
-    """Other forms and workloads, each measured once outside the headline's
-    timed region (CUDA events on the handle's stream)."""
+def extra_workloads(B, inputs, sptr, peaks):
+    """The other forms and workloads, each measured once outside the headline's
+    timed region (CUDA events on the handle's stream), each with its error
+    against the closed form and its roofline against the measured peaks."""
     import numpy as np
     import torch
 
     from oracle import reduced
     out = {}
     stream = torch.cuda.current_stream()
+    sms = peaks["sms"]
+    fp64, fp32 = peaks["fp64_fma_tflops"], peaks["fp32_fma_tflops"]
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -192,17 +205,29 @@ def extra_workloads(B, inputs, sptr):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1000.0, r
 
-    # precision forms at the full n = 29 workload (P error vs the closed form)
+    # precision forms at the full n = 29 workload (errors vs the closed form)
     inst = inputs.config_n29()
-    Pc = reduced.closed_form(inst.n, inst.M, inst.k)[0]
+    Pc, awc, _ = reduced.closed_form(inst.n, inst.M, inst.k)
     for dt in ("c64", "dw"):
         g = B.GroverMPS(inst.n, inst.marked, dtype=dt, apply=APPLY, chi_max=inst.chi_max, stream=sptr)
         sec, _ = timed(lambda: g.iterate(inst.k))
         p = g.prob_marked()
+        a = g.amplitude(inst.marked[0])
         bits = g.sample(4096, SAMPLE_SEED)
-        out[f"n29_{dt}"] = {"iterations_per_s": inst.k / sec, "P_marked": p, "P_err": p - Pc,
-                            "shots_4096_marked": int(np.sum(bits == inst.marked[0])),
-                            "dtype": {"c64": "c64 (FP64 QR/SVD)", "dw": "f32x2 double-word"}[dt]}
+        chi = g.stats()["max_bond"]
+        lin, con = flops_per_iter_parts(inst.n, chi, inst.M, APPLY)
+        ent = {"iterations_per_s": inst.k / sec, "P_marked": p, "P_err": p - Pc, "amp_err": abs(a - awc),
+               "shots_4096_marked": int(np.sum(bits == inst.marked[0])), "max_bond": chi}
+        if dt == "c64":
+            ent["dtype"] = "c64 storage and contraction, FP64 QR/SVD and bookkeeping"
+            ent["roofline"] = roofline_alu(inst.k * (lin + con), sec, fp64, "FP64 FMA", 1, sms)
+            ent["roofline"]["note"] = (f"FP64 QR/SVD {lin:.3g} + FP32 contraction {con:.3g} flops per iteration; "
+                                       "the FP64 part sets the bound")
+        else:
+            ent["dtype"] = "f32x2 double-word on the FP32 pipes"
+            ent["roofline"] = roofline_alu(inst.k * (lin + con), sec, fp32, "FP32 FMA", 1, sms)
+            ent["roofline"]["note"] = "algorithmic flops; each double-word flop costs several FP32 instructions"
+        out[f"n29_{dt}"] = ent
         g.close()
     # batched: the 512-instance workload with its full k_i = min(floor(pi/4
     # sqrt(2^n/M)), 4000); the autotuner's timed slices (k_i capped at 10) are
@@ -214,26 +239,53 @@ def extra_workloads(B, inputs, sptr):
     bt.set_threads(thr)
     sec, _ = timed(lambda: bt.run(use_graph=True))
     p, st, rc = bt.result()
-    errs = [abs(p[i] - reduced.closed_form(x.n, x.M, x.k)[0]) for i, x in enumerate(insts)]
+    errs, rel = [], []
+    flops = 0.0
+    busy, t0s, t1s, longest = {}, [], [], 0.0
+    bad_bonds = 0
+    for i, x in enumerate(insts):
+        P = reduced.closed_form(x.n, x.M, x.k)[0]
+        errs.append(abs(p[i] - P))
+        rel.append(abs(p[i] - P) / P)
+        s_ = bt.stats(i)
+        flops += x.k * algorithmic_flops_per_iter(x.n, s_["max_bond"], x.M, APPLY)
+        d = (s_["t_end_ns"] - s_["t_begin_ns"]) / 1e9
+        busy[s_["sm_id"]] = busy.get(s_["sm_id"], 0.0) + d
+        t0s.append(s_["t_begin_ns"])
+        t1s.append(s_["t_end_ns"])
+        longest = max(longest, d)
+        if s_["max_bond"] > x.M + 1:
+            bad_bonds += 1
+    span = (max(t1s) - min(t0s)) / 1e9
     tot = sum(x.k for x in insts)
-    out["batched_512_c64"] = {"iterations_per_s": tot / sec, "seconds": sec, "total_iterations": tot,
-                              "k": "full, min(floor(pi/4 sqrt(2^n/M)), 4000)", "threads": thr,
-                              "autotune": rec, "graph": True,
-                              "max_P_err": max(errs), "median_P_err": float(np.median(errs)),
-                              "instances_with_status": int((st != 0).sum())}
+    rl = roofline_alu(flops, sec, fp64, "FP64 FMA", sms, sms)
+    out["batched_512_c64"] = {
+        "iterations_per_s": tot / sec, "seconds": sec, "total_iterations": tot,
+        "k": "full, min(floor(pi/4 sqrt(2^n/M)), 4000)", "threads": thr, "autotune": rec, "graph": True,
+        "max_P_err": max(errs), "median_P_err": float(np.median(errs)), "max_P_rel_err": max(rel),
+        "instances_with_status": int((st != 0).sum()), "instances_above_rank_M_plus_1": bad_bonds,
+        "sm_busy": {"launch_span_s": span, "sms_used": len(busy),
+                    "mean_busy_frac": sum(busy.values()) / (sms * span),
+                    "longest_instance_s": longest,
+                    "total_instance_s": sum(busy.values())},
+        "roofline": rl}
     bt.close()
-    # multi-marked n = 40, M = 32 (short slice)
-    mi = inputs.config_multi_marked(k=5)
+    # multi-marked n = 40, M = 32, chi_max = 128, tol = 1e-12, full k = 1000
+    mi = inputs.config_multi_marked(k=1000)
     g = B.GroverMPS(mi.n, mi.marked, dtype="c128", apply=APPLY, chi_max=mi.chi_max, tol=mi.tol, stream=sptr)
-    g.iterate(1)
-    sec, _ = timed(lambda: g.iterate(4))
+    g.iterate(1)                                                   # warm-up iteration
+    g.reset()
+    sec, _ = timed(lambda: g.iterate(mi.k))
     p = g.prob_marked()
-    Pm = reduced.closed_form(mi.n, mi.M, 5)[0]
-    out["n40_M32_c128"] = {"iterations_per_s": 4 / sec, "k_slice": 5, "P_rel_err": (p - Pm) / Pm,
-                           "max_bond": g.stats()["max_bond"]}
+    Pm = reduced.closed_form(mi.n, mi.M, mi.k)[0]
+    chi = g.stats()["max_bond"]
+    out["n40_M32_c128"] = {"iterations_per_s": mi.k / sec, "k": mi.k, "seconds": sec, "P_marked": p,
+                           "P_closed_form": Pm, "P_rel_err": (p - Pm) / Pm, "max_bond": chi,
+                           "roofline": roofline_alu(mi.k * algorithmic_flops_per_iter(mi.n, chi, mi.M, APPLY),
+                                                    sec, fp64, "FP64 FMA", 1, sms)}
     g.close()
     # differentiable: n = 20, M = 4, K = 64, the batch of 64 phase vectors,
-    # forward + backward of all 64 side by side (one stream and host thread each)
+    # forward + backward of all 64
     from paper_2601_03832_gb300 import autograd as AG
     di, phi, psi = inputs.config_differentiable(B=64)
     AG.loss_and_grad_batch(di.n, di.marked, phi[:2], psi[:2])          # warm-up
@@ -246,28 +298,13 @@ def extra_workloads(B, inputs, sptr):
     for b in range(len(phi)):
         L, rphi, rpsi = reduced.loss_and_grad(di.n, di.M, phi[b], psi[b])
         worst = max(worst, abs(Ls[b] - L), float(np.abs(gphis[b] - rphi).max()), float(np.abs(gpsis[b] - rpsi).max()))
+    # forward K iterations, segment recompute K iterations, costate K steps
+    dflops = len(phi) * 3 * di.k * algorithmic_flops_per_iter(di.n, di.M + 1, di.M, APPLY)
     out["differentiable_n20_M4_K64"] = {"fwd_bwd_ms_per_vector": 1000 * sec / len(phi), "vectors": len(phi),
-                                        "wall_s": sec, "concurrent": True,
-                                        "max_err_vs_reduced_model": worst}
+                                        "wall_s": sec, "max_err_vs_reduced_model": worst,
+                                        "roofline": roofline_alu(dflops, sec, fp64, "FP64 FMA",
+                                                                 min(len(phi), sms), sms)}
     return out
-
-
-def batch_probe(count: int, kcap: int):
-    """One batched launch of the first `count` instances of the batched
-    workload with k_i capped at `kcap` (a small case for ncu captures)."""
-    import torch
-
-    from paper_2601_03832_gb300 import binding as B
-    from paper_2601_03832_gb300 import inputs
-    torch.cuda.set_device(0)
-    insts = inputs.config_batched(count=512)[:count]
-    for i in insts:
-        i.k = min(i.k, kcap)
-    b = B.GroverBatch(insts, dtype="c64", apply=APPLY)
-    b.set_threads(256)
-    b.run(use_graph=False)
-    p, st, rc = b.result()
-    print(json.dumps({"batch_probe": count, "k_cap": kcap, "status": int(rc), "instances_with_status": int((st != 0).sum())}))
 
 
 def run_reference(args):
@@ -290,6 +327,7 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": "iterations/s", "cores": 1, "kind": "oracle",
                              "sample": f"per step a {budget:.0f} s slice of the n=29 iterations (NumPy FP64 MPS oracle, "
                                        "1 thread); ms_per_step extrapolates the slice to k=18198"},
+            "ms_per_step_extrapolated": True,
             "e2e": {"value": v, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -302,14 +340,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other forms and workloads")
-    ap.add_argument("--k", type=int, default=K_ITERS, help=argparse.SUPPRESS)
-    ap.add_argument("--batch-probe", default=None, metavar="COUNT,KCAP",
-                    help="run one batched launch (complex64, fused, 256 threads) and exit (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.batch_probe:
-        return batch_probe(*[int(x) for x in args.batch_probe.split(",")])
 
     import numpy as np
     import torch
@@ -328,8 +361,10 @@ def main():
     B.load()
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
+    from paper_2601_03832_gb300 import peaks as PK
+    peaks = PK.measure()
     inst = inputs.config_n29()
-    k = args.k
+    k = inst.k
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     g = B.GroverMPS(inst.n, inst.marked, dtype="c128", apply=APPLY, chi_max=inst.chi_max, stream=sptr)
@@ -371,7 +406,7 @@ def main():
     e2e_ms = []
     h2d = 8 * inst.M                                         # marked strings
     d2h = 16 * inst.M + 16 + 8 * sum(SHOTS)                  # amplitudes, P, shots
-    for i in range(max(1, args.steps)):
+    for i in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ge = B.GroverMPS(inst.n, inst.marked, dtype="c128", apply=APPLY, chi_max=inst.chi_max, stream=sptr)
@@ -395,7 +430,14 @@ def main():
     chi = max(st["chi"])
     flops = k * algorithmic_flops_per_iter(inst.n, chi, inst.M, APPLY)
     kern_s = statistics.mean(kern_ms) / 1000.0
-    achieved = flops / kern_s / 1e12
+    roof = roofline_alu(flops, kern_s, peaks["fp64_fma_tflops"], "FP64 FMA", 1, peaks["sms"])
+    roof.update({"traffic": CAPTURE["traffic_bytes"], "kernel": "iterate_kernel<double,double2,double>",
+                 "algorithmic_flops_per_launch": flops, "kernel_ms": statistics.mean(kern_ms)})
+    if CAPTURE["fp64_pipe_share"] is not None:
+        roof["chain_bound"] = {"model": "FP64 issue bound: the instance's FP64 warp instructions back to back "
+                                        "on one SM sub-partition's pipe, as a share of the launch",
+                               "frac": CAPTURE["fp64_pipe_share"],
+                               "source": "ncu capture of the iterate kernel at n=29, k=50"}
     line = {
         "metric": "MPS Grover iterations/s (n=29, M=1, FP64)",
         "value": value, "unit": "iterations/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -410,17 +452,8 @@ def main():
                     "amp_closed_form": awc, "shots_4096_marked": int(np.sum(bits[0] == inst.marked[0])),
                     "shot_1": int(bits[1][0]), "max_bond": chi, "jacobi_sweeps_max": st["max_jacobi_sweeps"],
                     "discarded_weight": st["discarded_weight"]},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
-                     "chain_bound": {"model": "FP64 issue bound: the instance's FP64 warp instructions (~64 "
-                                              "cycles each on this part, two warps on two SM sub-partitions) "
-                                              "back to back on one pipe, as a share of the launch",
-                                     "frac": FP64_ISSUE_BOUND_FRAC,
-                                     "source": "ncu capture, profiles/iterate_kernel_n29_M1_fp64.md"},
-                     "kernel": "iterate_kernel<double,double2,double>",
-                     "algorithmic_flops_per_launch": flops, "kernel_ms": statistics.mean(kern_ms),
-                     "peak_source": "nominal FP64 rate of the part (recipe table), 1.25 TFLOP/s; one instance "
-                                    "runs on one of 152 SMs"},
+        "roofline": roof,
+        "peaks": peaks,
         "e2e": {"value": e2e_val, "unit": "iterations/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": statistics.mean(e2e_ms)},
         "gpu_launches": launches,
@@ -428,7 +461,7 @@ def main():
     clk_sum = clk.summary()
     line["clocks"] = clk_sum
     if not args.no_extras and ws == 1:
-        line["workloads"] = extra_workloads(B, inputs, sptr)
+        line["workloads"] = extra_workloads(B, inputs, sptr, peaks)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     g.close()

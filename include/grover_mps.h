@@ -119,6 +119,9 @@ typedef struct gmps_stats {
   int64_t jacobi_sweeps;    /* sweeps summed over all SVDs */
   int64_t svd_count;        /* SVDs performed */
   int device_status;        /* gmps_status reported by the device */
+  int sm_id;                /* SM that ran the instance's last iterate launch */
+  int64_t t_begin_ns;       /* device clock (ns) when that launch began ... */
+  int64_t t_end_ns;         /* ... and finished this instance */
 } gmps_stats;
 
 /* ------------------------------------------------------------------ */
@@ -235,10 +238,44 @@ gmps_status grover_mps_batch_result(gmps_batch_handle b, double* host_p,
 gmps_status grover_mps_batch_amplitude(gmps_batch_handle b, int i, uint64_t bits,
                                        double* re, double* im);
 
+/* Statistics of instance i of the batch (synchronises): bond table,
+ * discarded weight, Jacobi counters, device status, and the SM and device
+ * clock interval that ran it in the last grover_mps_batch_run. */
+gmps_status grover_mps_batch_stats(gmps_batch_handle b, int i, gmps_stats* out);
+
 /* Override the CTA size of the batched launch (autotuner hook); 0 = auto. */
 gmps_status grover_mps_batch_set_threads(gmps_batch_handle b, int threads);
 
 gmps_status grover_mps_batch_destroy(gmps_batch_handle b);
+
+/* ------------------------------------------------------------------ */
+/* Differentiable batch: many phase vectors of one problem at once.    */
+/* ------------------------------------------------------------------ */
+
+typedef struct gmps_diff_batch_ctx* gmps_diff_batch_handle;
+
+/* `count` phase vectors (phi_b, psi_b), b < count, of K iterations each for
+ * the problem in `cfg` (n, marked, dtype, apply, chi_max, tol, max_sweeps,
+ * threads, checkpoint_every as for a differentiable handle; its
+ * differentiable, max_iters and arena fields are ignored).  The loss is
+ * L_b = 1 - P_marked(G_K ... G_1 |s>) with G_j = D(psi_b,j) O(phi_b,j)
+ * (Sec. II, Eq. 3, phases generalised).  Allocates every vector's chain,
+ * checkpoints (every checkpoint_every iterations), segment-recompute chain
+ * and costate chain. */
+gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int K, void* cuda_stream,
+                                         gmps_diff_batch_handle* out);
+
+/* Forward and reverse sweep of all phase vectors: host_phi, host_psi are
+ * count x K row-major host arrays; outputs host_loss (count values of L_b)
+ * and host_gphi, host_gpsi (count x K, dL_b / dphi_b,j and dL_b / dpsi_b,j).
+ * Every stage runs as one launch over all vectors (one thread block per
+ * vector): the forward segments between checkpoints, the checkpoint copies,
+ * the projection mu_K = Pi_W psi_K, and for each segment (last first) the
+ * recompute from its checkpoint and the costate sweep.  Synchronises. */
+gmps_status grover_mps_diff_batch_run(gmps_diff_batch_handle b, const double* host_phi, const double* host_psi,
+                                      double* host_loss, double* host_gphi, double* host_gpsi);
+
+gmps_status grover_mps_diff_batch_destroy(gmps_diff_batch_handle b);
 
 /* Number of kernel launches this library has enqueued on any stream since
  * load (counts every <<<>>> launch and graph kernel node replay). */
@@ -250,14 +287,18 @@ int64_t grover_mps_launch_count(void);
 
 /* For callers that must not allocate device memory (no cudaMalloc/cudaFree
  * after start-up, or an allocator they may not touch): runs one FP64
- * (complex128) instance -- |+>^n, k iterations, the marked amplitudes --
- * entirely inside a fixed 2 MiB device array compiled into the library,
- * with no handle and no allocation of any kind.
+ * (complex128) instance -- |+>^n, k iterations, the marked amplitudes and
+ * the bond table -- entirely inside a fixed 2 MiB device array compiled into
+ * the library, with no handle and no device allocation of any kind.  Inputs
+ * are validated, planned and truncated exactly as grover_mps_create_ex does
+ * for dtype GMPS_C128 with the same apply, chi_max and tol (same statuses,
+ * same bonds).
  *   marked      host, M distinct strings < 2^n (copied during the call)
  *   apply       gmps_apply; chi_max, tol as in gmps_config
  *   dev_phi/psi device arrays of k phases, or NULL for pi
  *   p_marked    host output: sum_w |<w|psi>|^2
  *   amp_marked  host output, 2M doubles (re, im per marked string) or NULL
+ *   chi_out     host output, n+1 ints (bond dimensions chi_0..chi_n) or NULL
  * The call synchronises `cuda_stream`.  Instances whose chain needs more
  * than the array's 2 MiB return GMPS_ERR_CAPACITY.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) and
@@ -266,7 +307,7 @@ int64_t grover_mps_launch_count(void);
 gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int M, int apply, int chi_max,
                                    double tol, int64_t k, const double* dev_phi,
                                    const double* dev_psi, void* cuda_stream, double* p_marked,
-                                   double* amp_marked);
+                                   double* amp_marked, int* chi_out);
 
 #ifdef __cplusplus
 }

@@ -9,8 +9,6 @@ in libgrover_mps.so.
 """
 from __future__ import annotations
 
-from concurrent.futures import ThreadPoolExecutor
-
 import numpy as np
 import torch
 
@@ -46,36 +44,22 @@ def differentiable_handle(n, marked, K, dtype="c128", apply="fused", chi_max=Non
                              stream=stream)
 
 
-def loss_and_grad_batch(n, marked, phis, psis, dtype="c128", apply="fused", chi_max=None, checkpoint_every=8):
+def loss_and_grad_batch(n, marked, phis, psis, dtype="c128", apply="fused", chi_max=None, checkpoint_every=8,
+                        stream=None):
     """L = 1 - P_marked and its gradients for B independent phase vectors
-    (rows of phis, psis: B x K), all at once.  Each vector gets its own
-    handle and CUDA stream and is driven from its own host thread (the C
-    calls release the GIL), so the single-block launches of the B vectors
-    run side by side on different SMs.  Returns (L[B], dL/dphi[B, K],
-    dL/dpsi[B, K])."""
+    (rows of phis, psis: B x K), all at once through
+    grover_mps_diff_batch_run: the forward segments, checkpoint copies,
+    projection, segment recomputes and costate sweeps of the B vectors each
+    run as one launch (one thread block per vector).  Returns (L[B],
+    dL/dphi[B, K], dL/dpsi[B, K])."""
     phis = np.ascontiguousarray(phis, dtype=np.float64)
     psis = np.ascontiguousarray(psis, dtype=np.float64)
     nb, K = phis.shape
-    binding.load()
-    streams = [torch.cuda.Stream() for _ in range(nb)]
-    # handles are created up front: device allocations from many threads at
-    # once contend (measured slower than creating them in turn)
-    handles = [differentiable_handle(n, marked, K, dtype=dtype, apply=apply, chi_max=chi_max,
-                                     checkpoint_every=checkpoint_every, stream=s.cuda_stream) for s in streams]
-
-    def run(i):
-        h = handles[i]
-        h.iterate(K, phis[i], psis[i])
-        p = h.prob_marked()
-        gphi, gpsi = h.backward(-1.0)
-        return 1.0 - p, gphi, gpsi
-
+    if stream is None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    db = binding.DiffBatch(n, marked, nb, K, dtype=dtype, apply=apply, chi_max=chi_max,
+                           checkpoint_every=checkpoint_every, stream=stream)
     try:
-        # more concurrent single-block launches than SMs buy nothing
-        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        with ThreadPoolExecutor(max_workers=max(1, min(nb, sms))) as ex:
-            out = list(ex.map(run, range(nb)))
+        return db.run(phis, psis)
     finally:
-        for h in handles:
-            h.close()
-    return (np.array([o[0] for o in out]), np.stack([o[1] for o in out]), np.stack([o[2] for o in out]))
+        db.close()

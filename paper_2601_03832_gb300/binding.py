@@ -29,8 +29,15 @@ EXPORTS = [
     "grover_mps_prob_marked", "grover_mps_sample", "grover_mps_sample_device", "grover_mps_backward",
     "grover_mps_stats", "grover_mps_export", "grover_mps_destroy", "grover_mps_last_error",
     "grover_mps_batch_create", "grover_mps_batch_run", "grover_mps_batch_result",
-    "grover_mps_batch_amplitude", "grover_mps_batch_set_threads", "grover_mps_batch_destroy",
-    "grover_mps_launch_count", "grover_mps_run_noalloc",
+    "grover_mps_batch_amplitude", "grover_mps_batch_stats", "grover_mps_batch_set_threads",
+    "grover_mps_batch_destroy",
+    "grover_mps_launch_count", "grover_mps_run_noalloc", "grover_mps_diff_batch_create",
+    "grover_mps_diff_batch_run", "grover_mps_diff_batch_destroy",
+]
+# every symbol include/grover_sv.h declares
+SV_EXPORTS = [
+    "grover_sv_bytes", "grover_sv_create", "grover_sv_reset", "grover_sv_iterate", "grover_sv_amplitude",
+    "grover_sv_prob_marked", "grover_sv_export", "grover_sv_destroy",
 ]
 
 
@@ -45,7 +52,16 @@ class gmps_stats(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("n", C.c_int), ("chi", C.c_int * 65), ("max_bond", C.c_int),
                 ("log_norm", C.c_double), ("discarded_weight", C.c_double),
                 ("max_jacobi_sweeps", C.c_int), ("jacobi_sweeps", C.c_int64), ("svd_count", C.c_int64),
-                ("device_status", C.c_int)]
+                ("device_status", C.c_int), ("sm_id", C.c_int), ("t_begin_ns", C.c_int64),
+                ("t_end_ns", C.c_int64)]
+
+
+def _stats_dict(s, n):
+    return {"iterations": s.iterations, "chi": list(s.chi[: n + 1]), "max_bond": s.max_bond,
+            "log_norm": s.log_norm, "discarded_weight": s.discarded_weight,
+            "max_jacobi_sweeps": s.max_jacobi_sweeps, "jacobi_sweeps": s.jacobi_sweeps,
+            "svd_count": s.svd_count, "device_status": s.device_status, "sm_id": s.sm_id,
+            "t_begin_ns": s.t_begin_ns, "t_end_ns": s.t_end_ns}
 
 
 class GMPSError(RuntimeError):
@@ -87,9 +103,21 @@ def load():
         "grover_mps_batch_run": [vp, i32],
         "grover_mps_batch_result": [vp, P(f64), P(i32)],
         "grover_mps_batch_amplitude": [vp, i32, u64, P(f64), P(f64)],
+        "grover_mps_batch_stats": [vp, i32, P(gmps_stats)],
         "grover_mps_batch_set_threads": [vp, i32],
         "grover_mps_batch_destroy": [vp],
-        "grover_mps_run_noalloc": [i32, P(u64), i32, i32, i32, f64, i64, vp, vp, vp, P(f64), P(f64)],
+        "grover_mps_run_noalloc": [i32, P(u64), i32, i32, i32, f64, i64, vp, vp, vp, P(f64), P(f64), P(i32)],
+        "grover_mps_diff_batch_create": [P(gmps_config), i32, i32, vp, P(vp)],
+        "grover_mps_diff_batch_run": [vp, P(f64), P(f64), P(f64), P(f64), P(f64)],
+        "grover_mps_diff_batch_destroy": [vp],
+        "grover_sv_bytes": [i32, i32, P(C.c_size_t)],
+        "grover_sv_create": [i32, P(u64), i32, i32, vp, P(vp)],
+        "grover_sv_reset": [vp],
+        "grover_sv_iterate": [vp, i64, P(f64), P(f64)],
+        "grover_sv_amplitude": [vp, u64, P(f64), P(f64)],
+        "grover_sv_prob_marked": [vp, P(f64)],
+        "grover_sv_export": [vp, P(f64), C.c_size_t],
+        "grover_sv_destroy": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -203,10 +231,7 @@ class GroverMPS:
     def stats(self) -> dict:
         s = gmps_stats()
         _check(load().grover_mps_stats(self.h, C.byref(s)))
-        return {"iterations": s.iterations, "chi": list(s.chi[: self.n + 1]), "max_bond": s.max_bond,
-                "log_norm": s.log_norm, "discarded_weight": s.discarded_weight,
-                "max_jacobi_sweeps": s.max_jacobi_sweeps, "jacobi_sweeps": s.jacobi_sweeps,
-                "svd_count": s.svd_count, "device_status": s.device_status}
+        return _stats_dict(s, self.n)
 
     def export(self):
         """Site tensors as a list of complex128 arrays (chi_l, 2, chi_{l+1})."""
@@ -239,16 +264,107 @@ class GroverMPS:
 def run_noalloc(n, marked, k, apply="mpo", chi_max=4, tol=0.0, dev_phi=0, dev_psi=0, stream=None):
     """grover_mps_run_noalloc: one FP64 instance in the library's static device
     array, for callers that cannot allocate device memory.  Returns
-    (P_marked, amplitudes of the marked strings)."""
+    (P_marked, amplitudes of the marked strings, bond table chi_0..chi_n)."""
     lib = load()
     m = np.ascontiguousarray(np.asarray(marked, dtype=np.uint64))
     p = C.c_double()
     amps = np.zeros(2 * len(m))
+    chi = np.zeros(int(n) + 1, dtype=np.int32)
     _check(lib.grover_mps_run_noalloc(int(n), m.ctypes.data_as(C.POINTER(C.c_uint64)), len(m),
                                       APPLY[apply] if isinstance(apply, str) else int(apply), int(chi_max),
                                       float(tol), int(k), C.c_void_p(dev_phi or 0), C.c_void_p(dev_psi or 0),
-                                      C.c_void_p(stream or 0), C.byref(p), _dptr(amps)))
-    return p.value, amps[0::2] + 1j * amps[1::2]
+                                      C.c_void_p(stream or 0), C.byref(p), _dptr(amps),
+                                      chi.ctypes.data_as(C.POINTER(C.c_int))))
+    return p.value, amps[0::2] + 1j * amps[1::2], [int(x) for x in chi]
+
+
+class DiffBatch:
+    """Loss L = 1 - P_marked and its phase gradients for many phase vectors of
+    one problem (grover_mps_diff_batch_*): every stage of the forward and
+    reverse sweeps is one launch over all vectors."""
+
+    def __init__(self, n, marked, count, K, dtype="c128", apply="fused", chi_max=None, tol=0.0,
+                 checkpoint_every=8, threads=0, stream=None):
+        lib = load()
+        cfg, self._marked = make_config(n, marked, dtype=dtype, apply=apply,
+                                        chi_max=chi_max if chi_max else len(marked) + 1, tol=tol,
+                                        threads=threads, checkpoint_every=checkpoint_every)
+        h = C.c_void_p()
+        _check(lib.grover_mps_diff_batch_create(C.byref(cfg), int(count), int(K), C.c_void_p(stream or 0),
+                                                C.byref(h)))
+        self.h, self.count, self.K = h, int(count), int(K)
+
+    def run(self, phis, psis):
+        """phis, psis: (count, K).  Returns (L[count], dL/dphi, dL/dpsi)."""
+        ph = np.ascontiguousarray(phis, dtype=np.float64).reshape(self.count, self.K)
+        ps = np.ascontiguousarray(psis, dtype=np.float64).reshape(self.count, self.K)
+        loss = np.zeros(self.count)
+        gphi = np.zeros((self.count, self.K))
+        gpsi = np.zeros((self.count, self.K))
+        _check(load().grover_mps_diff_batch_run(self.h, _dptr(ph), _dptr(ps), _dptr(loss), _dptr(gphi),
+                                                _dptr(gpsi)))
+        return loss, gphi, gpsi
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().grover_mps_diff_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GroverSV:
+    """Iterative Grover on a dense statevector (grover_sv_*): complex128
+    ("c128") or complex64 ("c64") amplitudes in device memory."""
+
+    def __init__(self, n, marked, dtype="c128", stream=None):
+        lib = load()
+        m = np.ascontiguousarray(np.asarray(marked, dtype=np.uint64))
+        self.n, self.marked = n, [int(x) for x in m]
+        h = C.c_void_p()
+        _check(lib.grover_sv_create(int(n), m.ctypes.data_as(C.POINTER(C.c_uint64)), len(m),
+                                    DTYPES[dtype] if isinstance(dtype, str) else int(dtype),
+                                    C.c_void_p(stream or 0), C.byref(h)))
+        self.h = h
+
+    def reset(self):
+        _check(load().grover_sv_reset(self.h))
+
+    def iterate(self, k, phi=None, psi=None):
+        pa = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+        sa = None if psi is None else np.ascontiguousarray(psi, dtype=np.float64)
+        _check(load().grover_sv_iterate(self.h, int(k), None if pa is None else _dptr(pa),
+                                        None if sa is None else _dptr(sa)))
+
+    def amplitude(self, bits) -> complex:
+        re, im = C.c_double(), C.c_double()
+        _check(load().grover_sv_amplitude(self.h, C.c_uint64(int(bits)), C.byref(re), C.byref(im)))
+        return complex(re.value, im.value)
+
+    def prob_marked(self) -> float:
+        p = C.c_double()
+        _check(load().grover_sv_prob_marked(self.h, C.byref(p)))
+        return p.value
+
+    def export(self) -> np.ndarray:
+        buf = np.zeros(2 << self.n, dtype=np.float64)
+        _check(load().grover_sv_export(self.h, _dptr(buf), buf.size))
+        return buf.view(np.complex128)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().grover_sv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class GroverBatch:
@@ -277,6 +393,7 @@ class GroverBatch:
         _check(lib.grover_mps_batch_create(cnt, cfgs, ks.ctypes.data_as(C.POINTER(C.c_int64)), pp, ps,
                                            C.c_void_p(stream or 0), C.byref(h)))
         self.h, self.count, self.ks = h, cnt, ks
+        self.ns = [inst.n for inst in instances]
 
     def set_threads(self, threads):
         _check(load().grover_mps_batch_set_threads(self.h, int(threads)))
@@ -289,6 +406,11 @@ class GroverBatch:
         st = np.zeros(self.count, dtype=np.int32)
         rc = load().grover_mps_batch_result(self.h, _dptr(p), st.ctypes.data_as(C.POINTER(C.c_int)))
         return p, st, rc
+
+    def stats(self, i) -> dict:
+        s = gmps_stats()
+        _check(load().grover_mps_batch_stats(self.h, int(i), C.byref(s)))
+        return _stats_dict(s, self.ns[i])
 
     def amplitude(self, i, bits) -> complex:
         re, im = C.c_double(), C.c_double()

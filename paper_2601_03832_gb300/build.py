@@ -1,7 +1,10 @@
-"""Builds libgrover_mps.so in-tree for sm_103a with nvcc (no CMake).
+"""Builds the in-tree CUDA libraries for sm_103a with nvcc (no CMake).
 
-Each translation unit is compiled in parallel, then linked as a shared
-library next to this file.  Run: python -m paper_2601_03832_gb300.build
+libgrover_mps.so   the iterative-Grover engine behind include/grover_mps.h
+libgmps_peaks.so   peak-rate microbenchmarks behind include/gmps_peaks.h
+
+Every translation unit is compiled in parallel, then each library is linked
+next to this file.  Run: python -m paper_2601_03832_gb300.build
 """
 from __future__ import annotations
 
@@ -13,8 +16,10 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["gmps_kernels.cu", "gmps_capi.cu"]
+SOURCES = ["gmps_form_c128.cu", "gmps_form_c64.cu", "gmps_form_dw.cu", "gmps_launch.cu", "gmps_capi.cu", "gmps_sv.cu"]
 LIB = os.path.join(HERE, "libgrover_mps.so")
+PEAK_SOURCES = ["gmps_peaks.cu"]
+PEAK_LIB = os.path.join(HERE, "libgmps_peaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
@@ -26,16 +31,25 @@ def _nvcc() -> str:
     return "nvcc"
 
 
+def _stale(lib, deps):
+    if not os.path.exists(lib):
+        return True
+    t = os.path.getmtime(lib)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile and link both libraries if any source changed; returns the
+    engine library's path."""
     objdir = os.path.join(ROOT, "_build")
     os.makedirs(objdir, exist_ok=True)
-    srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    deps.append(os.path.join(ROOT, "include", "grover_mps.h"))
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
-        if all(os.path.getmtime(d) <= t for d in deps):
-            return LIB
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    headers += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
+    libs = [(LIB, [os.path.join(CSRC, x) for x in SOURCES]),
+            (PEAK_LIB, [os.path.join(CSRC, x) for x in PEAK_SOURCES])]
+    todo = [(lib, srcs) for lib, srcs in libs if force or _stale(lib, srcs + headers)]
+    if not todo:
+        return LIB
     nvcc = _nvcc()
 
     def compile_one(src):
@@ -48,14 +62,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    all_srcs = [src for _, srcs in todo for src in srcs]
+    with ThreadPoolExecutor(max_workers=len(all_srcs)) as ex:
+        objs = dict(zip(all_srcs, ex.map(compile_one, all_srcs)))
+    for lib, srcs in todo:
+        tmp = lib + ".tmp"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[objs[x] for x in srcs], "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -7,7 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <set>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -41,23 +41,38 @@ static gmps_status cuda_fail(cudaError_t e, const char* where) {
 
 static size_t a256(size_t x) { return (x + 255) / 256 * 256; }
 
-// eps of the rank rule sigma_i > max(tol, max(m,n) eps) sigma_0, set above
-// the rounding noise that a contraction + QR + Jacobi chain leaves in a
-// rank-deficient direction, so that the noise is never kept as a Schmidt
-// direction: FP32's unit for complex64, 2^-42 for double-word, and four FP64
-// units (2^-50) for FP64 -- a noise row of 2.7 units was measured on a 2 x 2
-// step, whose max(m,n) = 2 would otherwise put the threshold at 2 units.
-static double trunc_eps_for(int dtype) {
-  if (dtype == GMPS_C64_F64SVD) return 1.1920928955078125e-07;
-  if (dtype == GMPS_DW) return 2.2737367544323206e-13;
-  return 8.881784197001252e-16;
+// Rank rule sigma_i > max(tol, floor) sigma_0 (and the rank-revealing QR's
+// stop), with the floor set above the rounding noise that a contraction + QR
+// + Jacobi chain leaves in a rank-deficient direction, so that the noise is
+// never kept as a Schmidt direction:
+//  * FP64: max(m, n) times four units (2^-50) -- a noise row of 2.7 units was
+//    measured on a 2 x 2 step, whose max(m, n) = 2 would otherwise put the
+//    floor at 2 units;
+//  * double-word: max(m, n) 2^-42;
+//  * complex64 with FP64 QR/SVD: a fixed 2^-22.  Its noise is the FP32
+//    storage and contraction seen by FP64 linear algebra; rounding-noise
+//    singular values reached 2^-26.4 sigma_0 over 1500 iterations of an
+//    n = 36, M = 16 instance, while the marked component's Schmidt values
+//    start near 2^{1-n/2} (2^-17 at n = 36).  The storage-unit rule
+//    max(m, n) 2^-23 reached those values and truncated the marked component
+//    away at n = 36.
+struct RankRule {
+  double eps;
+  int dim;  // 1: floor = max(m, n) eps
+};
+static RankRule rank_rule_for(int dtype) {
+  if (dtype == GMPS_C64_F64SVD) return {2.384185791015625e-07, 0};
+  if (dtype == GMPS_DW) return {2.2737367544323206e-13, 1};
+  return {8.881784197001252e-16, 1};
 }
 
 // ---------------------------------------------------------------- sizing
+// Launch and storage plan of one instance (host only; fixed size, so that
+// planning allocates nothing).
 struct Plan {
   int chicap, xcap, threads, resident;
   size_t smem, site_elems, elem_bytes;
-  std::vector<long long> off;  // n+1
+  long long off[kMaxN + 1];  // slot offsets, n+1 used
 };
 
 static int xcap_for(int apply, int M, int chicap) {
@@ -81,12 +96,15 @@ static gmps_status validate(const gmps_config* c) {
   if (c->n < 64 && (uint64_t)c->M >= (1ull << c->n)) return fail(GMPS_ERR_ARG, "M must be < 2^n");
   if (c->M > kMaxMarked) return fail(GMPS_ERR_UNSUPPORTED, "M above the built maximum (64)");
   if (!c->marked) return fail(GMPS_ERR_ARG, "marked is NULL");
-  std::set<uint64_t> seen;
+  uint64_t sorted[kMaxMarked];
   for (int i = 0; i < c->M; ++i) {
     uint64_t w = c->marked[i];
     if (c->n < 64 && (w >> c->n) != 0) return fail(GMPS_ERR_ARG, "marked string has bits >= n");
-    if (!seen.insert(w).second) return fail(GMPS_ERR_ARG, "duplicate marked string");
+    sorted[i] = w;
   }
+  std::sort(sorted, sorted + c->M);
+  for (int i = 1; i < c->M; ++i)
+    if (sorted[i] == sorted[i - 1]) return fail(GMPS_ERR_ARG, "duplicate marked string");
   if (c->chi_max < 1) return fail(GMPS_ERR_ARG, "chi_max must be >= 1");
   if (!(c->tol >= 0.0) || !std::isfinite(c->tol)) return fail(GMPS_ERR_ARG, "tol must be finite and >= 0");
   if (c->dtype != GMPS_C128 && c->dtype != GMPS_C64_F64SVD && c->dtype != GMPS_DW)
@@ -115,7 +133,7 @@ static gmps_status make_plan_for(const gmps_config* c, bool allow_resident, Plan
     if (c->apply == GMPS_APPLY_MPO && xcap > 64) continue;
     P->chicap = chicap;
     P->xcap = xcap;
-    P->off.assign(c->n + 1, 0);
+    P->off[0] = 0;
     for (int l = 0; l < c->n; ++l) P->off[l + 1] = P->off[l] + slot_elems(l, c->n, xcap);
     P->site_elems = P->off[c->n];
     P->elem_bytes = eb;
@@ -177,6 +195,7 @@ struct gmps_ctx {
   double* d_rec = nullptr;         // every * (M+1) complex
   double* d_grad = nullptr;        // 2 * max_iters
   double* d_ph_all = nullptr;      // 2 * max_iters
+  AdjArgs* d_args = nullptr;       // [0] projection step, [1] segment steps
   char* diff_mem = nullptr;
   bool all_phases_explicit = true;
 };
@@ -214,7 +233,8 @@ static InstDesc base_desc(const gmps_ctx* h, const Slab& s) {
   d.max_sweeps = h->cfg.max_sweeps ? h->cfg.max_sweeps : kDefaultMaxSweeps;
   d.resident = h->plan.resident;
   d.tol = h->cfg.tol;
-  d.trunc_eps = trunc_eps_for(h->cfg.dtype);
+  d.trunc_eps = rank_rule_for(h->cfg.dtype).eps;
+  d.trunc_dim = rank_rule_for(h->cfg.dtype).dim;
   d.inv_sqrt_N = std::ldexp(1.0, -h->cfg.n / 2) * ((h->cfg.n & 1) ? std::sqrt(0.5) : 1.0);
   d.marked = h->d_marked;
   d.sites = s.d_sites;
@@ -225,7 +245,7 @@ static InstDesc base_desc(const gmps_ctx* h, const Slab& s) {
 
 static gmps_status upload_slab(gmps_ctx* h, const Slab& s) {
   InstDesc d = base_desc(h, s);
-  CUDA_TRY(cudaMemcpyAsync(s.d_off, h->plan.off.data(), sizeof(long long) * (h->cfg.n + 1),
+  CUDA_TRY(cudaMemcpyAsync(s.d_off, h->plan.off, sizeof(long long) * (h->cfg.n + 1),
                            cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaMemcpyAsync(s.d_desc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(launch_init(s.d_desc, 1, h->cfg.dtype, 64, h->stream));
@@ -324,7 +344,7 @@ gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps
     const int nck = h->max_iters / h->every + 1;
     const size_t sb = slab_bytes(&h->cfg, h->plan);
     const size_t bytes = sb * (nck + 2) + a256(sizeof(double) * 2 * (cfg->M + 1) * h->every) +
-                         2 * a256(sizeof(double) * 2 * h->max_iters);
+                         2 * a256(sizeof(double) * 2 * h->max_iters) + a256(sizeof(AdjArgs) * 2);
     cudaError_t e2 = cudaMalloc(&h->diff_mem, bytes);
     if (e2 != cudaSuccess) {
       grover_mps_destroy(h);
@@ -340,6 +360,8 @@ gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps
     h->d_grad = (double*)q;
     q += a256(sizeof(double) * 2 * h->max_iters);
     h->d_ph_all = (double*)q;
+    q += a256(sizeof(double) * 2 * h->max_iters);
+    h->d_args = (AdjArgs*)q;
     for (int j = 0; j < nck && !s; ++j) s = upload_slab(h, h->ckpt[j]);
     if (!s) s = upload_slab(h, h->work);
     if (!s) s = upload_slab(h, h->costate);
@@ -454,7 +476,7 @@ gmps_status grover_mps_iterate(gmps_handle h, int64_t k, const double* host_phi,
         return s;
       done += chunk;
       if ((pos + chunk) % h->every == 0)
-        CUDA_TRY(launch_copy_sites(h->main.d_desc, h->ckpt[(pos + chunk) / h->every].d_desc, h->cfg.dtype,
+        CUDA_TRY(launch_copy_sites(h->main.d_desc, h->ckpt[(pos + chunk) / h->every].d_desc, 1, h->cfg.dtype,
                                    h->stream));
     }
   } else if ((s = enqueue_iterate(h, k, dphi, dpsi, h->main))) {
@@ -535,16 +557,12 @@ gmps_status grover_mps_sample(gmps_handle h, int64_t shots, uint64_t seed, uint6
   return check_device(h);
 }
 
-gmps_status grover_mps_stats(gmps_handle h, gmps_stats* out) {
-  if (!h || !out) return fail(GMPS_ERR_ARG, "NULL argument");
-  DevStats ds;
-  CUDA_TRY(cudaMemcpyAsync(&ds, h->main.d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(cudaStreamSynchronize(h->stream));
+static void fill_stats(const DevStats& ds, int n, gmps_stats* out) {
   memset(out, 0, sizeof(*out));
   out->iterations = ds.iterations;
-  out->n = h->cfg.n;
+  out->n = n;
   int mb = 1;
-  for (int l = 0; l <= h->cfg.n; ++l) {
+  for (int l = 0; l <= n; ++l) {
     out->chi[l] = ds.chi[l];
     mb = std::max(mb, ds.chi[l]);
   }
@@ -555,6 +573,17 @@ gmps_status grover_mps_stats(gmps_handle h, gmps_stats* out) {
   out->jacobi_sweeps = ds.jacobi_sweeps;
   out->svd_count = ds.svd_count;
   out->device_status = ds.status;
+  out->sm_id = ds.sm;
+  out->t_begin_ns = (int64_t)ds.t_begin;
+  out->t_end_ns = (int64_t)ds.t_end;
+}
+
+gmps_status grover_mps_stats(gmps_handle h, gmps_stats* out) {
+  if (!h || !out) return fail(GMPS_ERR_ARG, "NULL argument");
+  DevStats ds;
+  CUDA_TRY(cudaMemcpyAsync(&ds, h->main.d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  fill_stats(ds, h->cfg.n, out);
   return GMPS_OK;
 }
 
@@ -615,18 +644,23 @@ gmps_status grover_mps_backward(gmps_handle h, double dL_dP, double* grad_phi, d
   CUDA_TRY(cudaMemcpyAsync(h->d_ph_all, h->phi_hist.data(), sizeof(double) * K, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaMemcpyAsync(h->d_ph_all + mi, h->psi_hist.data(), sizeof(double) * K, cudaMemcpyHostToDevice,
                            h->stream));
+  AdjArgs args[2];
+  args[0] = AdjArgs{nullptr, h->d_ph_all, h->d_ph_all + mi, h->d_grad, h->d_grad + mi, dL_dP};
+  args[1] = args[0];
+  args[1].rec = h->d_rec;
+  CUDA_TRY(cudaMemcpyAsync(h->d_args, args, sizeof(args), cudaMemcpyHostToDevice, h->stream));
   // mu_K = Pi_W psi_K on the costate chain
-  CUDA_TRY(launch_copy_sites(h->main.d_desc, h->costate.d_desc, h->cfg.dtype, h->stream));
-  CUDA_TRY(launch_adjoint(h->costate.d_desc, h->cfg.dtype, h->plan.threads, h->plan.smem, nullptr, K, K,
-                          h->d_ph_all, h->d_ph_all + mi, dL_dP, h->d_grad, h->d_grad + mi, 1, h->stream));
+  CUDA_TRY(launch_copy_sites(h->main.d_desc, h->costate.d_desc, 1, h->cfg.dtype, h->stream));
+  CUDA_TRY(launch_adjoint(h->costate.d_desc, h->d_args, 1, h->cfg.dtype, h->plan.threads, h->plan.smem, K, K, 1,
+                          h->stream));
   for (int64_t j = (K - 1) / h->every; j >= 0; --j) {
     const int64_t k_lo = j * h->every, k_hi = std::min<int64_t>(K, k_lo + h->every);
     // recompute the segment from its checkpoint, recording <w|psi> and <s|psi>
-    CUDA_TRY(launch_copy_sites(h->ckpt[j].d_desc, h->work.d_desc, h->cfg.dtype, h->stream));
+    CUDA_TRY(launch_copy_sites(h->ckpt[j].d_desc, h->work.d_desc, 1, h->cfg.dtype, h->stream));
     gmps_status s = enqueue_iterate(h, k_hi - k_lo, h->d_ph_all + k_lo, h->d_ph_all + mi + k_lo, h->work, h->d_rec);
     if (s) return s;
-    CUDA_TRY(launch_adjoint(h->costate.d_desc, h->cfg.dtype, h->plan.threads, h->plan.smem, h->d_rec, k_lo, k_hi,
-                            h->d_ph_all, h->d_ph_all + mi, dL_dP, h->d_grad, h->d_grad + mi, 0, h->stream));
+    CUDA_TRY(launch_adjoint(h->costate.d_desc, h->d_args + 1, 1, h->cfg.dtype, h->plan.threads, h->plan.smem, k_lo,
+                            k_hi, 0, h->stream));
   }
   CUDA_TRY(cudaMemcpyAsync(grad_phi, h->d_grad, sizeof(double) * K, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaMemcpyAsync(grad_psi, h->d_grad + mi, sizeof(double) * K, cudaMemcpyDeviceToHost, h->stream));
@@ -772,7 +806,8 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
     d.resident = 0;
     d.k = ks[i];
     d.tol = c.tol;
-    d.trunc_eps = trunc_eps_for(c.dtype);
+    d.trunc_eps = rank_rule_for(c.dtype).eps;
+    d.trunc_dim = rank_rule_for(c.dtype).dim;
     d.inv_sqrt_N = std::ldexp(1.0, -c.n / 2) * ((c.n & 1) ? std::sqrt(0.5) : 1.0);
     long long* off = (long long*)p;
     p += a256(sizeof(long long) * (c.n + 1));
@@ -786,7 +821,7 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
     d.marked = mk_;
     double* ph = (double*)p;
     p += a256(sizeof(double) * 2 * ks[i]);
-    e = cudaMemcpyAsync(off, P.off.data(), sizeof(long long) * (c.n + 1), cudaMemcpyHostToDevice, b->stream);
+    e = cudaMemcpyAsync(off, P.off, sizeof(long long) * (c.n + 1), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(mk_, c.marked, sizeof(uint64_t) * c.M, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess && host_phi && host_phi[i]) {
@@ -892,6 +927,16 @@ gmps_status grover_mps_batch_amplitude(gmps_batch_handle b, int i, uint64_t bits
   return GMPS_OK;
 }
 
+gmps_status grover_mps_batch_stats(gmps_batch_handle b, int i, gmps_stats* out) {
+  if (!b || !out || i < 0 || i >= b->count) return fail(GMPS_ERR_ARG, "bad argument");
+  const int q = b->pos[i];
+  DevStats ds;
+  CUDA_TRY(cudaMemcpyAsync(&ds, b->h[q].stats, sizeof(DevStats), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  fill_stats(ds, b->cfgs[i].n, out);
+  return GMPS_OK;
+}
+
 gmps_status grover_mps_batch_destroy(gmps_batch_handle b) {
   if (!b) return GMPS_OK;
   if (b->stream) cudaStreamSynchronize(b->stream);
@@ -904,3 +949,373 @@ gmps_status grover_mps_batch_destroy(gmps_batch_handle b) {
 }
 
 }  // extern "C"
+
+// ================================================================ differentiable batch
+// Every phase vector b has its chain (main), checkpoints, recompute chain
+// (work) and costate chain; descriptors of each role are contiguous arrays so
+// that one launch serves all vectors (iterate_kernel takes them from its work
+// queue, adjoint_kernel and copy_sites_kernel one block per vector).
+struct gmps_diff_batch_ctx {
+  gmps_config cfg{};
+  std::vector<uint64_t> marked;
+  Plan plan;
+  int count = 0, K = 0, every = 8, nseg = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char* mem = nullptr;
+  InstDesc* d_main = nullptr;   // count
+  InstDesc* d_work = nullptr;   // count
+  InstDesc* d_cost = nullptr;   // count
+  InstDesc* d_ckpt = nullptr;   // (nseg + 1) * count, checkpoint j of vector b at j * count + b
+  std::vector<InstDesc> h_main, h_work, h_cost, h_ckpt;
+  AdjArgs* d_args = nullptr;    // [0, count): projection, [count, 2 count): segments
+  DevStats* d_stats = nullptr;  // main, work, cost: 3 * count (checkpoint stats follow)
+  double* d_ph = nullptr;       // phi then psi, count x K each
+  double* d_grad = nullptr;     // dphi then dpsi, count x K each
+  double* d_rec = nullptr;      // count x every x (M + 1) complex
+  double* d_p = nullptr;        // count
+  int* d_queue = nullptr;
+  int grid = 1;
+};
+
+static gmps_status diff_launch_iterate(gmps_diff_batch_ctx* b, InstDesc* d_desc, std::vector<InstDesc>& h,
+                                       long long k, long long offset, bool record) {
+  const int M = b->cfg.M;
+  for (int i = 0; i < b->count; ++i) {
+    h[i].k = k;
+    h[i].phase_offset = offset;
+    h[i].rec = record ? b->d_rec + (size_t)i * b->every * (M + 1) * 2 : nullptr;
+  }
+  CUDA_TRY(cudaMemcpyAsync(d_desc, h.data(), sizeof(InstDesc) * b->count, cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream));
+  CUDA_TRY(launch_iterate(d_desc, b->count, b->d_queue, b->cfg.dtype, b->plan.threads, b->plan.smem, b->grid,
+                          b->stream));
+  return GMPS_OK;
+}
+
+extern "C" {
+
+gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int K, void* cuda_stream,
+                                         gmps_diff_batch_handle* out) {
+  if (!out) return fail(GMPS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  gmps_status s = validate(cfg);
+  if (s) return s;
+  if (count < 1 || K < 1) return fail(GMPS_ERR_ARG, "count and K must be >= 1");
+  gmps_diff_batch_ctx* b = new gmps_diff_batch_ctx();
+  b->cfg = *cfg;
+  b->marked.assign(cfg->marked, cfg->marked + cfg->M);
+  b->cfg.marked = b->marked.data();
+  b->count = count;
+  b->K = K;
+  b->every = cfg->checkpoint_every > 0 ? cfg->checkpoint_every : 8;
+  b->nseg = (K + b->every - 1) / b->every;
+  b->stream = (cudaStream_t)cuda_stream;
+  if (!b->stream) {
+    if (cudaStreamCreate(&b->stream) != cudaSuccess) {
+      delete b;
+      return fail(GMPS_ERR_CUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+  }
+  if ((s = make_plan_for(&b->cfg, true, &b->plan))) {
+    grover_mps_diff_batch_destroy(b);
+    return s;
+  }
+  const int M = cfg->M, n = cfg->n;
+  const int nslab = (3 + b->nseg + 1) * count;
+  const size_t site_b = a256(b->plan.site_elems * b->plan.elem_bytes);
+  const size_t bytes = a256(sizeof(long long) * (n + 1)) + a256(sizeof(unsigned long long) * M) +
+                       4 * a256(sizeof(InstDesc) * count) + a256(sizeof(InstDesc) * count * (b->nseg + 1)) +
+                       a256(sizeof(AdjArgs) * 2 * count) + a256(sizeof(DevStats) * nslab) +
+                       2 * a256(sizeof(double) * 2 * (size_t)count * K) +
+                       a256(sizeof(double) * 2 * (size_t)count * b->every * (M + 1)) +
+                       a256(sizeof(double) * count) + a256(sizeof(int)) + site_b * nslab;
+  cudaError_t e = cudaMalloc(&b->mem, bytes);
+  if (e != cudaSuccess) {
+    grover_mps_diff_batch_destroy(b);
+    return fail(GMPS_ERR_OOM, std::string("differentiable batch: ") + cudaGetErrorString(e));
+  }
+  char* p = b->mem;
+  long long* d_off = (long long*)p;          p += a256(sizeof(long long) * (n + 1));
+  unsigned long long* d_marked = (unsigned long long*)p;  p += a256(sizeof(unsigned long long) * M);
+  b->d_main = (InstDesc*)p;                   p += a256(sizeof(InstDesc) * count);
+  b->d_work = (InstDesc*)p;                   p += a256(sizeof(InstDesc) * count);
+  b->d_cost = (InstDesc*)p;                   p += a256(sizeof(InstDesc) * count);
+  p += a256(sizeof(InstDesc) * count);        // spare
+  b->d_ckpt = (InstDesc*)p;                   p += a256(sizeof(InstDesc) * count * (b->nseg + 1));
+  b->d_args = (AdjArgs*)p;                    p += a256(sizeof(AdjArgs) * 2 * count);
+  b->d_stats = (DevStats*)p;                  p += a256(sizeof(DevStats) * nslab);
+  b->d_ph = (double*)p;                       p += a256(sizeof(double) * 2 * (size_t)count * K);
+  b->d_grad = (double*)p;                     p += a256(sizeof(double) * 2 * (size_t)count * K);
+  b->d_rec = (double*)p;                      p += a256(sizeof(double) * 2 * (size_t)count * b->every * (M + 1));
+  b->d_p = (double*)p;                        p += a256(sizeof(double) * count);
+  b->d_queue = (int*)p;                       p += a256(sizeof(int));
+  char* sites = p;
+  const RankRule rr = rank_rule_for(cfg->dtype);
+  auto desc = [&](int slab) {
+    InstDesc d{};
+    d.n = n;
+    d.M = M;
+    d.apply = cfg->apply;
+    d.chi_max = cfg->chi_max;
+    d.chicap = b->plan.chicap;
+    d.xcap = b->plan.xcap;
+    d.max_sweeps = cfg->max_sweeps ? cfg->max_sweeps : kDefaultMaxSweeps;
+    d.resident = b->plan.resident;
+    d.tol = cfg->tol;
+    d.trunc_eps = rr.eps;
+    d.trunc_dim = rr.dim;
+    d.inv_sqrt_N = std::ldexp(1.0, -n / 2) * ((n & 1) ? std::sqrt(0.5) : 1.0);
+    d.marked = d_marked;
+    d.site_off = d_off;
+    d.stats = b->d_stats + slab;
+    d.sites = sites + site_b * slab;
+    return d;
+  };
+  b->h_main.resize(count);
+  b->h_work.resize(count);
+  b->h_cost.resize(count);
+  b->h_ckpt.resize((size_t)count * (b->nseg + 1));
+  for (int i = 0; i < count; ++i) {
+    b->h_main[i] = desc(i);
+    b->h_main[i].phi = b->d_ph + (size_t)i * K;
+    b->h_main[i].psi = b->d_ph + (size_t)(count + i) * K;
+    b->h_work[i] = desc(count + i);
+    b->h_work[i].phi = b->h_main[i].phi;
+    b->h_work[i].psi = b->h_main[i].psi;
+    b->h_cost[i] = desc(2 * count + i);
+  }
+  for (int j = 0; j <= b->nseg; ++j)
+    for (int i = 0; i < count; ++i) b->h_ckpt[(size_t)j * count + i] = desc(3 * count + j * count + i);
+  std::vector<AdjArgs> args(2 * count);
+  for (int i = 0; i < count; ++i) {
+    args[i] = AdjArgs{nullptr, b->h_main[i].phi, b->h_main[i].psi, b->d_grad + (size_t)i * K,
+                      b->d_grad + (size_t)(count + i) * K, -1.0};
+    args[count + i] = args[i];
+    args[count + i].rec = b->d_rec + (size_t)i * b->every * (M + 1) * 2;
+  }
+  e = cudaMemcpyAsync(d_off, b->plan.off, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_marked, b->marked.data(), sizeof(uint64_t) * M, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_args, args.data(), sizeof(AdjArgs) * 2 * count, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_work, b->h_work.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_cost, b->h_cost.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_ckpt, b->h_ckpt.data(), sizeof(InstDesc) * count * (b->nseg + 1),
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_main, b->h_main.data(), sizeof(InstDesc) * count, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    grover_mps_diff_batch_destroy(b);
+    return cuda_fail(e, "differentiable batch upload");
+  }
+  int dev = 0, nsm = 0, smem_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  int per_sm = std::max(1, (int)(smem_sm / (b->plan.smem + 1024)));
+  per_sm = std::min(per_sm, std::max(1, 2048 / b->plan.threads));
+  b->grid = std::min(count, nsm * per_sm);
+  *out = b;
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_diff_batch_run(gmps_diff_batch_handle b, const double* host_phi, const double* host_psi,
+                                      double* host_loss, double* host_gphi, double* host_gpsi) {
+  if (!b || !host_phi || !host_psi || !host_loss || !host_gphi || !host_gpsi)
+    return fail(GMPS_ERR_ARG, "NULL argument");
+  const size_t ck = (size_t)b->count * b->K;
+  for (size_t i = 0; i < ck; ++i)
+    if (!std::isfinite(host_phi[i]) || !std::isfinite(host_psi[i])) return fail(GMPS_ERR_ARG, "non-finite phase");
+  const int c = b->count, dt = b->cfg.dtype;
+  CUDA_TRY(cudaMemcpyAsync(b->d_ph, host_phi, sizeof(double) * ck, cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(b->d_ph + ck, host_psi, sizeof(double) * ck, cudaMemcpyHostToDevice, b->stream));
+  // forward: |s> on every chain and checkpoint 0, then segment by segment
+  CUDA_TRY(launch_init(b->d_main, c, dt, 64, b->stream));
+  CUDA_TRY(launch_init(b->d_ckpt, c, dt, 64, b->stream));
+  CUDA_TRY(launch_init(b->d_work, c, dt, 64, b->stream));
+  CUDA_TRY(launch_init(b->d_cost, c, dt, 64, b->stream));
+  gmps_status s;
+  for (int j = 0; j < b->nseg; ++j) {
+    const long long lo = (long long)j * b->every, hi = std::min<long long>(b->K, lo + b->every);
+    if ((s = diff_launch_iterate(b, b->d_main, b->h_main, hi - lo, lo, false))) return s;
+    if (j + 1 < b->nseg)
+      CUDA_TRY(launch_copy_sites(b->d_main, b->d_ckpt + (size_t)(j + 1) * c, c, dt, b->stream));
+  }
+  CUDA_TRY(launch_batch_prob(b->d_main, c, dt, b->d_p, b->stream));
+  // reverse: mu_K = Pi_W psi_K, then the segments last to first
+  CUDA_TRY(launch_copy_sites(b->d_main, b->d_cost, c, dt, b->stream));
+  CUDA_TRY(launch_adjoint(b->d_cost, b->d_args, c, dt, b->plan.threads, b->plan.smem, b->K, b->K, 1, b->stream));
+  for (int j = b->nseg - 1; j >= 0; --j) {
+    const long long lo = (long long)j * b->every, hi = std::min<long long>(b->K, lo + b->every);
+    CUDA_TRY(launch_copy_sites(b->d_ckpt + (size_t)j * c, b->d_work, c, dt, b->stream));
+    if ((s = diff_launch_iterate(b, b->d_work, b->h_work, hi - lo, lo, true))) return s;
+    CUDA_TRY(launch_adjoint(b->d_cost, b->d_args + c, c, dt, b->plan.threads, b->plan.smem, lo, hi, 0, b->stream));
+  }
+  std::vector<double> p(c);
+  std::vector<DevStats> st(3 * c);
+  CUDA_TRY(cudaMemcpyAsync(p.data(), b->d_p, sizeof(double) * c, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(host_gphi, b->d_grad, sizeof(double) * ck, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(host_gpsi, b->d_grad + ck, sizeof(double) * ck, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(st.data(), b->d_stats, sizeof(DevStats) * 3 * c, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < c; ++i) host_loss[i] = 1.0 - p[i];
+  for (int i = 0; i < 3 * c; ++i)
+    if (st[i].status) return fail((gmps_status)st[i].status, "a chain of the differentiable batch reported an error");
+  return GMPS_OK;
+}
+
+gmps_status grover_mps_diff_batch_destroy(gmps_diff_batch_handle b) {
+  if (!b) return GMPS_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->mem) cudaFree(b->mem);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return GMPS_OK;
+}
+
+}  // extern "C"
+
+// =====================================================================
+// Allocation-free entry point (grover_mps_run_noalloc).
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// host process that forbids cudaMalloc after start-up (real-time or
+// certified services that size every buffer up front), plugins loaded into a
+// process whose allocator they must not touch, or callers that run while the
+// device heap is deliberately exhausted.  For them this entry point runs a
+// whole instance (init, k iterations, marked amplitudes, bond table) in a
+// fixed file-scope device array instead of a handle's arena.  It calls no
+// cudaMalloc, cudaFree or other allocating routine.  It plans, validates and
+// truncates exactly as grover_mps_create_ex does for a complex128 instance
+// (same validate, make_plan_for and rank rule), so both give the same bonds.
+//
+// The array below is a device symbol: in host code its name is only a
+// host-side stand-in, never a device address.  Its address is fetched with
+// cudaGetSymbolAddress once per device (with that device current) by the
+// first call on that device; that first call should therefore come before
+// any stream capture.  Every GPU that loads this library holds the array
+// (kNoAllocScratchBytes) until the process exits.  All calls share it and
+// it keeps the last call's contents; each call re-initialises everything it
+// reads (descriptor, offsets, statistics, chain).  Calls whose GPU work
+// overlaps (different streams or threads without ordering) race on it.
+// =====================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 2u << 20;  // 2 MiB per device
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64];
+bool g_noalloc_ready[64];
+
+// Device address of g_noalloc_scratch on the current device (set-up on the
+// first call per device).
+cudaError_t noalloc_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ready[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = p;
+    g_noalloc_ready[dev] = true;
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int M, int apply, int chi_max,
+                                              double tol, int64_t k, const double* dev_phi,
+                                              const double* dev_psi, void* cuda_stream, double* p_marked,
+                                              double* amp_marked, int* chi_out) {
+  gmps_config c{};
+  c.n = n;
+  c.M = M;
+  c.marked = marked;
+  c.dtype = GMPS_C128;
+  c.apply = apply;
+  c.chi_max = chi_max;
+  c.tol = tol;
+  gmps_status s = validate(&c);
+  if (s) return s;
+  if (!p_marked) return fail(GMPS_ERR_ARG, "p_marked is NULL");
+  if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
+  Plan P;
+  if ((s = make_plan_for(&c, true, &P))) return s;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+  // carve the static array like a handle's slab
+  const size_t site_bytes = P.site_elems * P.elem_bytes;
+  const size_t o_desc = 0, o_off = a256(sizeof(InstDesc));
+  const size_t o_stats = o_off + a256(sizeof(long long) * (n + 1));
+  const size_t o_marked = o_stats + a256(sizeof(DevStats));
+  const size_t o_amp = o_marked + a256(sizeof(uint64_t) * M);
+  const size_t o_sites = o_amp + a256(sizeof(double) * 2 * M);
+  const size_t need = o_sites + a256(site_bytes);
+  if (need > kNoAllocScratchBytes)
+    return fail(GMPS_ERR_CAPACITY, "instance needs " + std::to_string(need) +
+                                       " bytes of static scratch; grover_mps_run_noalloc holds " +
+                                       std::to_string(kNoAllocScratchBytes));
+  void* base = nullptr;
+  cudaError_t e = noalloc_scratch_address(&base);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+  unsigned char* b = (unsigned char*)base;
+  const RankRule rr = rank_rule_for(GMPS_C128);
+  InstDesc d{};
+  d.n = n;
+  d.M = M;
+  d.apply = apply;
+  d.chi_max = chi_max;
+  d.chicap = P.chicap;
+  d.xcap = P.xcap;
+  d.max_sweeps = kDefaultMaxSweeps;
+  d.resident = P.resident;
+  d.k = k;
+  d.phase_offset = 0;
+  d.tol = tol;
+  d.trunc_eps = rr.eps;
+  d.trunc_dim = rr.dim;
+  d.inv_sqrt_N = std::ldexp(1.0, -n / 2) * ((n & 1) ? std::sqrt(0.5) : 1.0);
+  d.marked = (const unsigned long long*)(b + o_marked);
+  d.phi = dev_phi;
+  d.psi = dev_psi;
+  d.sites = b + o_sites;
+  d.site_off = (const long long*)(b + o_off);
+  d.stats = (DevStats*)(b + o_stats);
+  const InstDesc* d_desc = (const InstDesc*)(b + o_desc);
+  double* d_amp = (double*)(b + o_amp);
+  // everything the kernels read is rewritten here: the array keeps the
+  // previous call's contents
+  CUDA_TRY(cudaMemcpyAsync(b + o_desc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(b + o_off, P.off, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(cudaMemcpyAsync(b + o_marked, marked, sizeof(uint64_t) * M, cudaMemcpyHostToDevice, stream));
+  CUDA_TRY(launch_init(d_desc, 1, GMPS_C128, 64, stream));  // statistics and the |+>^n chain
+  if (k > 0) CUDA_TRY(launch_iterate(d_desc, 1, nullptr, GMPS_C128, P.threads, P.smem, 1, stream));
+  CUDA_TRY(launch_amplitudes(d_desc, 0, GMPS_C128, (const unsigned long long*)(b + o_marked), M, d_amp, stream));
+  double amps[2 * kMaxMarked];
+  DevStats ds;
+  CUDA_TRY(cudaMemcpyAsync(amps, d_amp, sizeof(double) * 2 * M, cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaMemcpyAsync(&ds, b + o_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  if (ds.status != 0)
+    return fail((gmps_status)ds.status, "device reported an error (status " + std::to_string(ds.status) + ")");
+  double p = 0.0;
+  for (int i = 0; i < M; ++i) p += amps[2 * i] * amps[2 * i] + amps[2 * i + 1] * amps[2 * i + 1];
+  *p_marked = p;
+  if (amp_marked)
+    for (int i = 0; i < 2 * M; ++i) amp_marked[i] = amps[i];
+  if (chi_out)
+    for (int l = 0; l <= n; ++l) chi_out[l] = ds.chi[l];
+  return GMPS_OK;
+}

@@ -1,4 +1,6 @@
-// Kernels of the iterative-Grover MPS engine for sm_103a.
+#pragma once
+// Device code of the iterative-Grover MPS engine for sm_103a (included by
+// one gmps_form_*.cu per arithmetic form, which instantiates it).
 //
 // One thread block owns one instance for a whole launch and applies all of
 // its Grover iterations without returning to the host (Sec. III-A: the
@@ -22,18 +24,10 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
-#include <cstdio>
 
-#include <atomic>
-
-#include "gmps_dw.cuh"
-#include "gmps_internal.h"
+#include "gmps_forms.h"
 
 namespace gmps {
-
-static std::atomic<long long> g_launches{0};
-void count_launch(long long n) { g_launches += n; }
-long long launches_so_far() { return g_launches.load(); }
 
 // ------------------------------------------------------------------ complex
 template <class T>
@@ -194,6 +188,18 @@ __device__ __forceinline__ Grp make_grp(int G) {
   return g;
 }
 
+// Device clock in ns and the SM id, for the per-instance busy-time record.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int sm_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return (int)r;
+}
+
 // ----------------------------------------------------------- device state
 template <class T, class S>
 struct Blk {
@@ -314,17 +320,6 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
   T floor2 = 0;
   int rank = pmax;
   for (int j = 0; j < pmax; ++j) {
-#ifdef GMPS_CHECK
-    if (threadIdx.x == 0) {
-      for (int c = j; c < ncol; ++c) {
-        double a = 0;
-        for (int i = j; i < m; ++i) a += (double)abs2(A[i * lda + c]);
-        if (fabs(a - (double)cn[c]) > 1e-12 * (1.0 + a))
-          printf("CNCHECK m=%d ncol=%d j=%d c=%d cn=%.15e actual=%.15e\n", m, ncol, j, c, (double)cn[c], a);
-      }
-    }
-    __syncthreads();
-#endif
     if (threadIdx.x == 0) {
       // pivot: largest remaining norm (compared through exact FP32 images)
       int best = j;
@@ -394,15 +389,6 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
         T a2 = abs2(x0);
         cx<T> b = mk<T>(0, 0);
         T t = 0;
-#ifdef GMPS_CHECK
-        {
-          double a = 0;
-          for (int i = j; i < m; ++i) a += (double)abs2(A[i * lda + j]);
-          if (fabs(a - (double)s) > 1e-12 * (1.0 + a))
-            printf("HHCHECK j=%d s=%.15e actual=%.15e x0=(%.6e,%.6e)\n", j, (double)s, a, (double)x0.re,
-                   (double)x0.im);
-        }
-#endif
         if (s > K<T>::tiny2()) {
           T inv = rsqrt(s);
           T nrm = s * inv;
@@ -446,18 +432,6 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
       if (act && g.lg == 0) cn[c] = s2;
     }
     __syncthreads();
-#ifdef GMPS_CHECK
-    if (threadIdx.x == 0) {
-      for (int jj = 0; jj <= j; ++jj) {
-        double v2 = 0;
-        for (int i = jj; i < m; ++i) v2 += (double)abs2(A[i * lda + jj]);
-        const double t = (double)tau[jj];
-        if (t != 0.0 && fabs(v2 * t - 2.0) > 1e-10)
-          printf("STEPCHECK after step %d: reflector %d off (%.12f) best=%d\n", j, jj, v2 * t, ctl[0]);
-      }
-    }
-    __syncthreads();
-#endif
   }
   return rank;
 }
@@ -778,26 +752,20 @@ __device__ void expand_absorb(Blk<T, S>& B, int l, int r, int xl, int xr, int mo
 }
 
 // ------------------------------------------------------------- sweeps
-#ifdef GMPS_PROF
-__device__ unsigned long long g_prof[16];
-#define PROF_T0 long long _pt = clock64();
-#define PROF_MARK(i)                                                   \
-  do {                                                                 \
-    __syncthreads();                                                   \
-    if (threadIdx.x == 0 && blockIdx.x == 0) {                         \
-      long long _n = clock64();                                        \
-      atomicAdd(&g_prof[i], (unsigned long long)(_n - _pt));           \
-      _pt = _n;                                                        \
-    }                                                                  \
-    __syncthreads();                                                   \
-  } while (0)
-#else
-#define PROF_T0
-#define PROF_MARK(i)
-#endif
 template <class T>
 __device__ __forceinline__ void set_status(int* misc, int code) {
   if (misc[0] == 0) misc[0] = code;
+}
+
+// Relative floor of the rank rule for an m x n matrix: singular values (and
+// rank-revealing QR pivots) at or below floor * sigma_0 are dropped.  Either
+// max(m, n) eps (the forms whose linear algebra runs in the storage type's
+// precision) or a fixed eps (the complex64 form, whose FP64 QR and SVD see
+// FP32-stored tensors: its rounding noise stays far below a fixed floor while
+// max(m, n) 2^-23 would reach the marked component's Schmidt values).
+template <class T, class S>
+__device__ __forceinline__ T rank_floor(const Blk<T, S>& B, int m, int n) {
+  return B.misc[5] ? (T)max(m, n) * B.tmisc[0] : B.tmisc[0];
 }
 
 #include "gmps_tiny.cuh"
@@ -807,7 +775,12 @@ __device__ __forceinline__ void set_status(int* misc, int code) {
 // (or (A_s[:,0,:] + A_s[:,1,:]) E / sqrt 2 for |+>^n).  A group of G lanes per
 // target (G a power of two covering every bond), lane lg holding E[lg]; after
 // site 0 lane 0 of each group holds <target|psi>.  Same quantity as
-// chain_targets, accumulated from the other end.
+// chain_targets, accumulated from the other end.  Both are called with
+// CR = T, the precision of the QR/SVD: these overlaps set the coefficients
+// of the next Grover step (its rotation in the {|w>, |r>} plane), so the
+// complex64 form reads its FP32 tensors but accumulates in FP64 (an FP32
+// chain product of n sites carries ~n 2^-24 relative error into every
+// iteration's rotation).
 template <class T, class S, class CR>
 __device__ __forceinline__ void env_fold(Blk<T, S>& B, int s, int nt, int G, cx<CR>& E) {
   const int lane = threadIdx.x & 31, lg = lane & (G - 1), base = lane & ~(G - 1);
@@ -862,7 +835,6 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       tiny_q_store<T, S>(tbuf_regs<T>(B.tbuf, site & 1)[threadIdx.x & 31], meta[1], meta[0], B.slot(site));
     }
   };
-  PROF_T0
   for (int l = 0; l < n; ++l) {
     const int xl = xb(l), xr = xb(l + 1);
     if (xr > d.xcap || xl > d.xcap) {
@@ -878,7 +850,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
         const cx<T> w0 = (c < xr && i < m)
                              ? expand_elem<T, S, CR>(B, l, i >> 1, i & 1, c, xl, mode, op, D, lbnd, cpsi, nt)
                              : mk<T>(0, 0);
-        const T fl = (T)max(m, xr) * B.tmisc[0];
+        const T fl = rank_floor(B, m, xr);
         cx<T> a;
         const int pt = tiny_qr_factor<T>(w0, m, xr, fl * fl, B.Rp, a);
         if (offload) {  // warp 1 forms Q during the next step
@@ -895,7 +867,6 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
         flush_q(pend);
       }
       __syncthreads();
-      PROF_MARK(1);
       pend = offload ? l : -1;
       r = B.qb[l + 1];
       continue;
@@ -906,95 +877,28 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       pend = -1;
     }
     expand_absorb<T, S, CR>(B, l, r, xl, xr, mode, op, D, lbnd, cpsi, nt);
-    PROF_MARK(0);
     if (l == n - 1) {
       for (int e = threadIdx.x; e < m; e += blockDim.x) st(dst + e, B.W[e]);
       if (threadIdx.x == 0) B.qb[n] = 1;
       __syncthreads();
       break;
     }
-#ifdef GMPS_TRACE
-    if (threadIdx.x == 0 && blockIdx.x == 0 && l < 3) {
-      printf("qr l=%d m=%d xr=%d W:", l, m, xr);
-      for (int t = 0; t < m * xr; ++t) printf(" (%.4e,%.4e)", (double)B.W[t].re, (double)B.W[t].im);
-      printf("\n");
-    }
-    __syncthreads();
-#endif
-#ifdef GMPS_CHECK
-    __shared__ double2 chkW[64 * 32];
-    for (int e = threadIdx.x; e < m * xr && e < 64 * 32; e += blockDim.x)
-      chkW[e] = make_double2((double)B.W[e].re, (double)B.W[e].im);
-    __syncthreads();
-#endif
     int p;
     {
-      const T fl = (T)max(m, xr) * B.tmisc[0];
+      const T fl = rank_floor(B, m, xr);
       p = qr_rank_revealing<T>(B.W, m, xr, xr, B.tau, B.beta, B.qperm, B.qcn, B.misc + 8, fl * fl);
     }
     if (p < 1) p = 1;
-#ifdef GMPS_CHECK
-    if (threadIdx.x == 0) {
-      for (int jj = 0; jj < p; ++jj) {
-        double v2 = 0;
-        for (int i = jj; i < m; ++i) v2 += (double)abs2(B.W[i * xr + jj]);
-        const double t = (double)B.tau[jj];
-        if (t != 0.0 && fabs(v2 * t - 2.0) > 1e-10)
-          printf("REFLCHECK l=%d m=%d xr=%d j=%d |v|^2*tau=%.12f tau=%.6e |beta|=%.6e\n", l, m, xr, jj, v2 * t, t,
-                 sqrt((double)abs2(B.beta[jj])));
-      }
-    }
-    __syncthreads();
-#endif
-    PROF_MARK(1);
     // R P^T -> Rp (p x xr, ld xr): column c of the pivoted R is original column perm[c]
     for (int e = threadIdx.x; e < p * xr; e += blockDim.x) {
       const int i = e / xr, c = e % xr;
       B.Rp[i * xr + B.qperm[c]] = (c > i) ? B.W[i * xr + c] : (c == i ? B.beta[i] : mk<T>(0, 0));
     }
     __syncthreads();
-    PROF_MARK(2);
     qr_form_q<T>(B.W, m, p, xr, B.tau);
-    PROF_MARK(3);
-#ifdef GMPS_CHECK
-    if (threadIdx.x == 0 && m * xr <= 64 * 32) {
-      double eo = 0, er = 0;
-      for (int a = 0; a < p; ++a)
-        for (int b2 = 0; b2 < p; ++b2) {
-          double re = 0, im = 0;
-          for (int i = 0; i < m; ++i) {
-            const double ar = (double)B.W[i * xr + a].re, ai = (double)B.W[i * xr + a].im;
-            const double br = (double)B.W[i * xr + b2].re, bi = (double)B.W[i * xr + b2].im;
-            re += ar * br + ai * bi;
-            im += ar * bi - ai * br;
-          }
-          eo = fmax(eo, fabs(re - (a == b2)) + fabs(im));
-        }
-      for (int i = 0; i < m; ++i)
-        for (int c2 = 0; c2 < xr; ++c2) {
-          double re = 0, im = 0;
-          for (int a = 0; a < p; ++a) {
-            const double qr_ = (double)B.W[i * xr + a].re, qi = (double)B.W[i * xr + a].im;
-            const double rr_ = (double)B.Rp[a * xr + c2].re, ri = (double)B.Rp[a * xr + c2].im;
-            re += qr_ * rr_ - qi * ri;
-            im += qr_ * ri + qi * rr_;
-          }
-          er = fmax(er, fabs(re - chkW[i * xr + c2].x) + fabs(im - chkW[i * xr + c2].y));
-        }
-      if (eo > 1e-12 || er > 1e-12) {
-        printf("QRCHECK l=%d m=%d xr=%d orth=%.3e recon=%.3e\n", l, m, xr, eo, er);
-        for (int i = 0; i < m; ++i) {
-          for (int c2 = 0; c2 < xr; ++c2) printf(" (%.17g,%.17g)", chkW[i * xr + c2].x, chkW[i * xr + c2].y);
-          printf("\n");
-        }
-      }
-    }
-    __syncthreads();
-#endif
     for (int e = threadIdx.x; e < m * p; e += blockDim.x) st(dst + e, B.W[(e / p) * xr + (e % p)]);
     if (threadIdx.x == 0) B.qb[l + 1] = p;
     __syncthreads();
-    PROF_MARK(4);
     r = p;
   }
   if (n == 1) {
@@ -1020,12 +924,11 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
   if (threadIdx.x == 0) B.US[0] = mk<T>(1, 0);
   __syncthreads();
   int kr = 1;  // bond to the right of the current site after truncation
-  const T eps_rule = B.tmisc[0];
   const T tol_rule = B.tmisc[1];
   // target environments (warp 1): E holds E_{folded}; sites >= folded are in
   const int envG = pow2_cap32(d.chicap);
   const bool warp1 = threadIdx.x >= 32 && threadIdx.x < 64;
-  cx<CR> E = mk<CR>((threadIdx.x & (envG - 1)) == 0 ? (CR)1 : (CR)0, 0);
+  cx<T> E = mk<T>((threadIdx.x & (envG - 1)) == 0 ? (T)1 : (T)0, 0);
   int folded = n;
   for (int l = n - 1; l >= 1; --l) {
     const int rl = B.qb[l], rr = B.qb[l + 1];
@@ -1035,15 +938,14 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       if (threadIdx.x < 32)
         tiny_svd_step<T, S, CR>(B, l, rl, rr, kr);
       else if (env_nt > 0 && warp1 && folded == l + 2)
-        env_fold<T, S, CR>(B, l + 1, env_nt, envG, E);  // site l+1 is final
+        env_fold<T, S, T>(B, l + 1, env_nt, envG, E);  // site l+1 is final
       __syncthreads();
-      PROF_MARK(7);
       if (env_nt > 0 && folded == l + 2) folded = l + 1;
       kr = B.misc[4];
       continue;
     }
     if (env_nt > 0 && folded == l + 2) {  // the block step needs every thread
-      if (warp1) env_fold<T, S, CR>(B, l + 1, env_nt, envG, E);
+      if (warp1) env_fold<T, S, T>(B, l + 1, env_nt, envG, E);
       __syncthreads();
       folded = l + 1;
     }
@@ -1055,7 +957,6 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       B.Mat[e] = cvt<T>(acc);
     }
     __syncthreads();
-    PROF_MARK(5);
     // noise floor for skipping rotations: (max(m,n) eps / 4)^2 times the
     // squared Frobenius norm of the matrix, which the sweep conserves up to
     // truncation -- measured once, at its first site
@@ -1067,19 +968,11 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const T f = (T)max(rl, c) * eps_rule * (T)0.25f;
+      const T f = rank_floor(B, rl, c) * (T)0.25f;
       B.tmisc[8] = B.tmisc[9] * f * f;
     }
     __syncthreads();
-    PROF_MARK(6);
-#ifdef GMPS_CHECK
-    __shared__ double2 chkM[48 * 48];
-    for (int e = threadIdx.x; e < rl * c && e < 48 * 48; e += blockDim.x)
-      chkM[e] = make_double2((double)B.Mat[e].re, (double)B.Mat[e].im);
-    __syncthreads();
-#endif
     const int sw = jacobi_rows<T>(B.Mat, rl, c, c, B.U, rl, d.max_sweeps, K<T>::jtolf(), B.tmisc[8]);
-    PROF_MARK(7);
     // row norms -> sigma, ranks -> perm
     {
       const int G = pow2_cap32(c);
@@ -1112,7 +1005,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       B.misc[3] += 1;
       // sigma_t > max(tol, max(m,n) eps) sigma_0, compared as squares
       const T s0 = B.sig[B.perm[0]];
-      const T fr = fmax(tol_rule, (T)max(rl, c) * eps_rule);
+      const T fr = fmax(tol_rule, rank_floor(B, rl, c));
       const T thr2 = fr * fr * s0;
       int k = 0;
       T tot = 0, kept = 0;
@@ -1132,18 +1025,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       B.misc[4] = k;
     }
     __syncthreads();
-    PROF_MARK(8);
     const int k = B.misc[4];
-#ifdef GMPS_TRACE
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-      printf("svd l=%d rl=%d c=%d kr=%d sw=%d k=%d sig:", l, rl, c, kr, sw, k);
-      for (int t = 0; t < rl; ++t) printf(" %.6e", (double)B.sig[B.perm[t]]);
-      printf(" | Mat0:");
-      for (int t = 0; t < c; ++t) printf(" (%.4e,%.4e)", (double)B.Mat[t].re, (double)B.Mat[t].im);
-      printf("\n");
-    }
-    __syncthreads();
-#endif
     // new site l = rows of V^dag (k x 2 x kr); US_l = U^dag[:, perm] * sigma (rl x k)
     // 1/sigma of each kept row from one rsqrt of sigma^2 (qcn is free here)
     for (int t = threadIdx.x; t < k; t += blockDim.x) B.qcn[t] = rsqrt(B.sig[B.perm[t]]);
@@ -1164,43 +1046,6 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     }
     if (threadIdx.x == 0) B.chi[l] = k;
     __syncthreads();
-    PROF_MARK(9);
-#ifdef GMPS_CHECK
-    if (threadIdx.x == 0) {
-      double eo = 0, er = 0;
-      for (int a = 0; a < k; ++a)
-        for (int b2 = 0; b2 < k; ++b2) {
-          double re = 0, im = 0;
-          for (int j = 0; j < c; ++j) {
-            const cx<T> x = ld<T>(dst + a * c + j), y = ld<T>(dst + b2 * c + j);
-            re += (double)x.re * (double)y.re + (double)x.im * (double)y.im;
-            im += (double)x.re * (double)y.im - (double)x.im * (double)y.re;
-          }
-          eo = fmax(eo, fabs(re - (a == b2)) + fabs(im));
-        }
-      for (int i = 0; i < rl; ++i)
-        for (int j = 0; j < c; ++j) {
-          double re = 0, im = 0;
-          for (int t = 0; t < k; ++t) {
-            const cx<T> u = B.US[i * k + t], v = ld<T>(dst + t * c + j);
-            re += (double)u.re * (double)v.re - (double)u.im * (double)v.im;
-            im += (double)u.re * (double)v.im + (double)u.im * (double)v.re;
-          }
-          if (rl * c <= 48 * 48)
-            er = fmax(er, fabs(re - chkM[i * c + j].x) + fabs(im - chkM[i * c + j].y));
-        }
-      if (eo > 1e-12 || er > 1e-12) {
-        printf("SVDCHECK l=%d rl=%d c=%d k=%d sw=%d orth=%.3e recon=%.3e sig:", l, rl, c, k, sw, eo, er);
-        for (int t = 0; t < rl; ++t) printf(" %.6e", (double)B.sig[B.perm[t]]);
-        printf("\n");
-        for (int i = 0; i < rl; ++i) {
-          for (int j = 0; j < c; ++j) printf(" (%.17g,%.17g)", (double)B.Mat[i * c + j].re, (double)B.Mat[i * c + j].im);
-          printf("\n");
-        }
-      }
-    }
-    __syncthreads();
-#endif
     kr = k;
   }
   // ------------------------------------------------ site 0 and renormalisation
@@ -1233,7 +1078,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
   }
   if (env_nt > 0) {  // sites folded..1 are final, site 0 just renormalised
     if (warp1) {
-      for (int s = folded - 1; s >= 0; --s) env_fold<T, S, CR>(B, s, env_nt, envG, E);
+      for (int s = folded - 1; s >= 0; --s) env_fold<T, S, T>(B, s, env_nt, envG, E);
       const int lane = threadIdx.x & 31;
       if ((lane & (envG - 1)) == 0 && lane / envG < env_nt) B.amps[lane / envG] = cvt<T>(E);
     }
@@ -1327,6 +1172,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
     __syncthreads();
     if (idx >= count) break;
     if (count == 1 && blockIdx.x != 0) break;
+    const unsigned long long t_begin = global_ns();
     const InstDesc& d = descs[idx];
     const int n = d.n;
     size_t site_bytes = 0;
@@ -1380,6 +1226,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
       B.dmisc[0] = ds->log_norm;
       B.dmisc[1] = ds->discarded;
       B.tmisc[0] = (T)d.trunc_eps;
+      B.misc[5] = d.trunc_dim;
       B.tmisc[1] = (T)d.tol;
       B.tmisc[2] = (T)0;
     }
@@ -1402,7 +1249,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
           B.tplus[t] = t == M;
         }
         __syncthreads();
-        if (!amps_ready) chain_targets<T, S, CR>(B, M + 1);
+        if (!amps_ready) chain_targets<T, S, T>(B, M + 1);
         for (int t = threadIdx.x; t <= M; t += blockDim.x) {
           d.rec[(it * (M + 1) + t) * 2] = (double)B.amps[t].re;
           d.rec[(it * (M + 1) + t) * 2 + 1] = (double)B.amps[t].im;
@@ -1444,7 +1291,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
           B.tplus[t] = 0;
         }
         __syncthreads();
-        chain_targets<T, S, CR>(B, M);
+        chain_targets<T, S, T>(B, M);
         for (int t = threadIdx.x; t < M; t += blockDim.x) B.tcoef[t] = cmul(em1, B.amps[t]);
         __syncthreads();
         sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(1, 0), M);
@@ -1455,7 +1302,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
           B.tplus[0] = 1;
         }
         __syncthreads();
-        chain_targets<T, S, CR>(B, 1);
+        chain_targets<T, S, T>(B, 1);
         if (threadIdx.x == 0) B.tcoef[0] = cmul(opsi, B.amps[0]);
         __syncthreads();
         sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), 1);
@@ -1467,9 +1314,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
         }
         __syncthreads();
         if (!amps_ready) {
-          PROF_T0
-          chain_targets<T, S, CR>(B, M + 1);
-          PROF_MARK(10);
+          chain_targets<T, S, T>(B, M + 1);
         }
         if (threadIdx.x == 0) {
           cx<T> sum = mk<T>(0, 0);
@@ -1502,6 +1347,9 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
       ds->svd_count += B.misc[3];
       ds->log_norm = B.dmisc[0];
       ds->discarded = B.dmisc[1] + (double)B.tmisc[2];
+      ds->t_begin = t_begin;
+      ds->t_end = global_ns();
+      ds->sm = sm_id();
     }
     __syncthreads();
     if (count == 1) break;
@@ -1532,7 +1380,7 @@ __device__ void adjoint_two_steps(Blk<T, S>& B, const double* rec, long long k, 
   __syncthreads();
   const double cp = B.dmisc[2], sp = B.dmisc[3], cs = B.dmisc[4], ss = B.dmisc[5];
   // <s|mu_k> of the normalised chain, scale lambda = e^{log norm}
-  chain_targets<T, S, CR>(B, 1);
+  chain_targets<T, S, T>(B, 1);
   double smr = 0, smi = 0;  // <s|mu_k> (thread 0)
   if (threadIdx.x == 0) {
     const double lam = exp(B.dmisc[0]);
@@ -1550,7 +1398,7 @@ __device__ void adjoint_two_steps(Blk<T, S>& B, const double* rec, long long k, 
     B.tplus[t] = 0;
   }
   __syncthreads();
-  chain_targets<T, S, CR>(B, M);
+  chain_targets<T, S, T>(B, M);
   if (threadIdx.x == 0) {
     const double lam = exp(B.dmisc[0]);
     const double* S_ = rec + (k - 1 - k_lo) * (M + 1) * 2;
@@ -1594,13 +1442,21 @@ __device__ void adjoint_two_steps(Blk<T, S>& B, const double* rec, long long k, 
 // the arena is sized for the split form); the costate's norm is carried by
 // the chain's log-norm.  rec holds
 // the forward chain's marked amplitudes and <s|psi_{k-1}> for k-1 = k_lo..k_hi-1.
-// The gradients are written scaled by `scale` (dL/dP).
+// The gradients are written scaled by `scale` (dL/dP).  One thread block per
+// costate chain: block b works on descs[b] with the arguments args[b] (a batch
+// of phase vectors of one problem runs as one launch).
 template <class T, class S, class CR>
-__global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, const double* rec, long long k_lo,
-                                                       long long k_hi, const double* phi, const double* psi,
-                                                       double scale, double* gphi, double* gpsi, int project) {
+__global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, const AdjArgs* args, long long k_lo,
+                                                       long long k_hi, int project) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const InstDesc& d = descs[0];
+  const InstDesc& d = descs[blockIdx.x];
+  const AdjArgs& aa = args[blockIdx.x];
+  const double* rec = aa.rec;
+  const double* phi = aa.phi;
+  const double* psi = aa.psi;
+  const double scale = aa.scale;
+  double* gphi = aa.gphi;
+  double* gpsi = aa.gpsi;
   const int n = d.n, M = d.M;
   size_t site_bytes = d.resident ? (size_t)d.site_off[n] * sizeof(S) : 0;
   const SmemPlan P = make_plan(n, M, d.xcap, d.chicap, sizeof(T), site_bytes);
@@ -1652,6 +1508,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
     B.dmisc[0] = project ? 0.0 : ds->log_norm;
     B.dmisc[1] = ds->discarded;
     B.tmisc[0] = (T)d.trunc_eps;
+    B.misc[5] = d.trunc_dim;
     B.tmisc[1] = (T)d.tol;
     B.tmisc[2] = (T)0;
   }
@@ -1673,7 +1530,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
   bool amps_ready = false;
   if (project) {
     // mu_K = sum_w psi_K(w) |w>: a direct sum without the chain's own block
-    chain_targets<T, S, CR>(B, M);
+    chain_targets<T, S, T>(B, M);
     for (int t = threadIdx.x; t < M; t += blockDim.x) B.tcoef[t] = B.amps[t];
     __syncthreads();
     sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(0, 0), M, env_nt);
@@ -1685,7 +1542,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
       continue;
     }
     // <w|mu_k> and <s|mu_k> of the normalised chain (scale lambda = e^{log norm})
-    if (!amps_ready) chain_targets<T, S, CR>(B, M + 1);
+    if (!amps_ready) chain_targets<T, S, T>(B, M + 1);
     if (threadIdx.x == 0) {
       double sp, cp, ss, cs;
       sincos(phi[k - 1], &sp, &cp);
@@ -1916,9 +1773,12 @@ __global__ void sample_kernel(const InstDesc* descs, int inst, long long shots, 
   if (margin) margin[shot] = mg;
 }
 
-// Copy the chain of one instance into another slab (checkpoints).
+// Copy the chain of instance src[i] into the slab of dst[i] (checkpoints),
+// i = blockIdx.y.
 template <class S>
-__global__ void copy_sites_kernel(const InstDesc* src, const InstDesc* dst) {
+__global__ void copy_sites_kernel(const InstDesc* srcs, const InstDesc* dsts) {
+  const InstDesc* src = srcs + blockIdx.y;
+  const InstDesc* dst = dsts + blockIdx.y;
   const long long total = src->site_off[src->n];
   const S* a = (const S*)src->sites;
   S* b = (S*)dst->sites;
@@ -1937,31 +1797,16 @@ __global__ void copy_sites_kernel(const InstDesc* src, const InstDesc* dst) {
 }
 
 // ------------------------------------------------------------ launchers
-size_t storage_bytes(int dtype) { return dtype == 1 ? sizeof(float2) : (dtype == 2 ? sizeof(dw2) : sizeof(double2)); }
-size_t linalg_real_bytes(int dtype) { return dtype == 2 ? sizeof(dw) : sizeof(double); }
-
-int max_smem_optin() {
-  int dev = 0, v = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return v;
-}
-
-cudaError_t launch_init(const InstDesc* d_desc, int count, int dtype, int threads, cudaStream_t stream) {
-  (void)threads;
-  if (dtype == 1)
-    init_kernel<float2><<<count, 64, 0, stream>>>(d_desc, count);
-  else if (dtype == 2)
-    init_kernel<dw2><<<count, 64, 0, stream>>>(d_desc, count);
-  else
-    init_kernel<double2><<<count, 64, 0, stream>>>(d_desc, count);
+template <class T, class S, class CR>
+cudaError_t FormLaunch<T, S, CR>::init(const InstDesc* d_desc, int count, cudaStream_t stream) {
+  init_kernel<S><<<count, 64, 0, stream>>>(d_desc, count);
   count_launch(1);
   return cudaGetLastError();
 }
 
 template <class T, class S, class CR>
-static cudaError_t launch_iter_t(const InstDesc* d_desc, int count, int* d_queue, int threads, size_t smem,
-                                 int grid, cudaStream_t stream) {
+cudaError_t FormLaunch<T, S, CR>::iterate(const InstDesc* d_desc, int count, int* d_queue, int threads, size_t smem,
+                                          int grid, cudaStream_t stream) {
   auto k = iterate_kernel<T, S, CR>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1970,67 +1815,39 @@ static cudaError_t launch_iter_t(const InstDesc* d_desc, int count, int* d_queue
   return cudaGetLastError();
 }
 
-cudaError_t launch_iterate(const InstDesc* d_desc, int count, int* d_queue, int dtype, int threads,
-                           size_t smem, int grid, cudaStream_t stream) {
-  if (dtype == 1) return launch_iter_t<double, float2, float>(d_desc, count, d_queue, threads, smem, grid, stream);
-  if (dtype == 2) return launch_iter_t<dw, dw2, dw>(d_desc, count, d_queue, threads, smem, grid, stream);
-  return launch_iter_t<double, double2, double>(d_desc, count, d_queue, threads, smem, grid, stream);
-}
-
 template <class T, class S, class CR>
-static cudaError_t launch_adj_t(const InstDesc* d_mu, int threads, size_t smem, const double* rec, long long k_lo,
-                                long long k_hi, const double* phi, const double* psi, double scale, double* gphi,
-                                double* gpsi, int project, cudaStream_t stream) {
+cudaError_t FormLaunch<T, S, CR>::adjoint(const InstDesc* d_mu, const AdjArgs* d_args, int count, int threads,
+                                          size_t smem, long long k_lo, long long k_hi, int project,
+                                          cudaStream_t stream) {
   auto k = adjoint_kernel<T, S, CR>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<1, threads, smem, stream>>>(d_mu, rec, k_lo, k_hi, phi, psi, scale, gphi, gpsi, project);
+  k<<<count, threads, smem, stream>>>(d_mu, d_args, k_lo, k_hi, project);
   count_launch(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(const InstDesc* d_mu, int dtype, int threads, size_t smem, const double* rec,
-                           long long k_lo, long long k_hi, const double* phi, const double* psi, double scale,
-                           double* gphi, double* gpsi, int project, cudaStream_t stream) {
-  if (dtype == 1)
-    return launch_adj_t<double, float2, float>(d_mu, threads, smem, rec, k_lo, k_hi, phi, psi, scale, gphi, gpsi,
-                                               project, stream);
-  if (dtype == 2)
-    return launch_adj_t<dw, dw2, dw>(d_mu, threads, smem, rec, k_lo, k_hi, phi, psi, scale, gphi, gpsi, project,
-                                     stream);
-  return launch_adj_t<double, double2, double>(d_mu, threads, smem, rec, k_lo, k_hi, phi, psi, scale, gphi, gpsi,
-                                               project, stream);
-}
-
-cudaError_t launch_amplitudes(const InstDesc* d_desc, int inst, int dtype, const unsigned long long* d_bits,
-                              int nbits, double* d_out, cudaStream_t stream) {
+template <class T, class S, class CR>
+cudaError_t FormLaunch<T, S, CR>::amplitudes(const InstDesc* d_desc, int inst, const unsigned long long* d_bits,
+                                             int nbits, double* d_out, cudaStream_t stream) {
   const int warps = 4;
   const int grid = (nbits + warps - 1) / warps;
-  if (dtype == 1)
-    amplitude_kernel<float2><<<grid, 32 * warps, 0, stream>>>(d_desc, inst, d_bits, nbits, d_out);
-  else if (dtype == 2)
-    amplitude_kernel<dw2><<<grid, 32 * warps, 0, stream>>>(d_desc, inst, d_bits, nbits, d_out);
-  else
-    amplitude_kernel<double2><<<grid, 32 * warps, 0, stream>>>(d_desc, inst, d_bits, nbits, d_out);
+  amplitude_kernel<S><<<grid, 32 * warps, 0, stream>>>(d_desc, inst, d_bits, nbits, d_out);
   count_launch(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_prob(const InstDesc* d_desc, int count, int dtype, double* d_p, cudaStream_t stream) {
-  if (dtype == 1)
-    batch_prob_kernel<float2><<<count, 128, 0, stream>>>(d_desc, count, d_p);
-  else if (dtype == 2)
-    batch_prob_kernel<dw2><<<count, 128, 0, stream>>>(d_desc, count, d_p);
-  else
-    batch_prob_kernel<double2><<<count, 128, 0, stream>>>(d_desc, count, d_p);
+template <class T, class S, class CR>
+cudaError_t FormLaunch<T, S, CR>::batch_prob(const InstDesc* d_desc, int count, double* d_p, cudaStream_t stream) {
+  batch_prob_kernel<S><<<count, 128, 0, stream>>>(d_desc, count, d_p);
   count_launch(1);
   return cudaGetLastError();
 }
 
-template <class S>
-static cudaError_t launch_sample_s(const InstDesc* d_desc, int inst, int chmax, long long shots,
-                                   unsigned long long seed, unsigned long long* d_bits, double* d_margin,
-                                   cudaStream_t stream) {
+template <class T, class S, class CR>
+cudaError_t FormLaunch<T, S, CR>::sample(const InstDesc* d_desc, int inst, int chmax, long long shots,
+                                         unsigned long long seed, unsigned long long* d_bits, double* d_margin,
+                                         cudaStream_t stream) {
   const int threads = 128;
   const long long grid = (shots + threads - 1) / threads;
   if (chmax <= 4)
@@ -2045,204 +1862,12 @@ static cudaError_t launch_sample_s(const InstDesc* d_desc, int inst, int chmax, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_sample(const InstDesc* d_desc, int inst, int dtype, int chmax, long long shots,
-                          unsigned long long seed, unsigned long long* d_bits, double* d_margin,
-                          cudaStream_t stream) {
-  if (dtype == 1) return launch_sample_s<float2>(d_desc, inst, chmax, shots, seed, d_bits, d_margin, stream);
-  if (dtype == 2) return launch_sample_s<dw2>(d_desc, inst, chmax, shots, seed, d_bits, d_margin, stream);
-  return launch_sample_s<double2>(d_desc, inst, chmax, shots, seed, d_bits, d_margin, stream);
-}
-
-cudaError_t launch_copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int dtype, cudaStream_t stream) {
-  if (dtype == 1)
-    copy_sites_kernel<float2><<<32, 256, 0, stream>>>(d_src, d_dst);
-  else if (dtype == 2)
-    copy_sites_kernel<dw2><<<32, 256, 0, stream>>>(d_src, d_dst);
-  else
-    copy_sites_kernel<double2><<<32, 256, 0, stream>>>(d_src, d_dst);
+template <class T, class S, class CR>
+cudaError_t FormLaunch<T, S, CR>::copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int count,
+                                             cudaStream_t stream) {
+  copy_sites_kernel<S><<<dim3(count > 1 ? 4 : 32, count), 256, 0, stream>>>(d_src, d_dst);
   count_launch(1);
   return cudaGetLastError();
 }
 
 }  // namespace gmps
-
-// =====================================================================
-// Allocation-free entry point (grover_mps_run_noalloc).
-//
-// Some callers cannot allocate device memory at all: code running inside
-// another runtime's allocator-free region (a real-time or safety-certified
-// host process that forbids cudaMalloc after start-up), plugins loaded into
-// a process whose allocator they must not touch, or callers that run while
-// the device heap is deliberately exhausted.  For them this entry point runs
-// a whole instance (init, k iterations, marked amplitudes) in a fixed
-// file-scope device array instead of a handle's arena.  It calls no
-// cudaMalloc, cudaFree or other allocating routine.
-//
-// The array below is a device symbol: in host code its name is only a
-// host-side stand-in, never a device address.  Its address is fetched with
-// cudaGetSymbolAddress once per device (with that device current) by the
-// first call on that device; that first call should therefore come before
-// any stream capture.  Every GPU that loads this library holds the array
-// (kNoAllocScratchBytes) until the process exits.  All calls share it and
-// it keeps the last call's contents; each call re-initialises everything it
-// reads (descriptor, offsets, statistics, chain).  Calls whose GPU work
-// overlaps (different streams or threads without ordering) race on it.
-// =====================================================================
-#include <mutex>
-#include <string>
-
-#include "../../include/grover_mps.h"
-
-namespace gmps {
-
-constexpr size_t kNoAllocScratchBytes = 2u << 20;  // 2 MiB per device
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-void set_last_error(const std::string& msg);  // gmps_capi.cu
-
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[64];
-static bool g_noalloc_ready[64];
-
-// Device address of g_noalloc_scratch on the current device (set-up on the
-// first call per device).
-static cudaError_t noalloc_scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ready[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = p;
-    g_noalloc_ready[dev] = true;
-  }
-  *out = g_noalloc_addr[dev];
-  return cudaSuccess;
-}
-
-static size_t noalloc_a256(size_t x) { return (x + 255) / 256 * 256; }
-
-}  // namespace gmps
-
-extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int M, int apply, int chi_max,
-                                              double tol, int64_t k, const double* dev_phi,
-                                              const double* dev_psi, void* cuda_stream, double* p_marked,
-                                              double* amp_marked) {
-  using namespace gmps;
-  auto fail = [](gmps_status s, const std::string& m) {
-    set_last_error(m);
-    return s;
-  };
-  if (n < 1 || n > 64) return fail(GMPS_ERR_ARG, "n must be in [1, 64]");
-  if (M < 1 || M > kMaxMarked || (n < 64 && (uint64_t)M >= (1ull << n)))
-    return fail(GMPS_ERR_ARG, "M must be in [1, min(2^n - 1, 64)]");
-  if (!marked || !p_marked) return fail(GMPS_ERR_ARG, "marked and p_marked must not be NULL");
-  for (int i = 0; i < M; ++i) {
-    if (n < 64 && (marked[i] >> n)) return fail(GMPS_ERR_ARG, "marked string has bits >= n");
-    for (int j = 0; j < i; ++j)
-      if (marked[j] == marked[i]) return fail(GMPS_ERR_ARG, "duplicate marked string");
-  }
-  if (apply < 0 || apply > 2) return fail(GMPS_ERR_ARG, "apply must be 0, 1 or 2");
-  if (chi_max < 1) return fail(GMPS_ERR_ARG, "chi_max must be >= 1");
-  if (!(tol >= 0.0) || !isfinite(tol)) return fail(GMPS_ERR_ARG, "tol must be finite and >= 0");
-  if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
-  cudaStream_t stream = (cudaStream_t)cuda_stream;
-
-  // plan (FP64 form): bond capacity, expanded bond, slots
-  int chicap = chi_max < M + 3 ? chi_max : M + 3;
-  long long half = 1;
-  for (int i = 0; i < n / 2 && half < chicap; ++i) half *= 2;
-  if (half < chicap) chicap = (int)half;
-  const int xcap = apply == 0 ? (M + 1) * chicap : (apply == 1 ? chicap + M : chicap + M + 1);
-  if (apply == 0 && xcap > 64) return fail(GMPS_ERR_UNSUPPORTED, "MPO contraction needs (M+1)*chi <= 64");
-  long long off[kMaxN + 1];
-  off[0] = 0;
-  for (int l = 0; l < n; ++l) off[l + 1] = off[l] + slot_elems(l, n, xcap);
-  const size_t site_bytes = (size_t)off[n] * sizeof(double2);
-  const size_t o_desc = 0, o_off = noalloc_a256(sizeof(InstDesc));
-  const size_t o_stats = o_off + noalloc_a256(sizeof(long long) * (n + 1));
-  const size_t o_marked = o_stats + noalloc_a256(sizeof(DevStats));
-  const size_t o_amp = o_marked + noalloc_a256(sizeof(uint64_t) * M);
-  const size_t o_sites = o_amp + noalloc_a256(sizeof(double) * 2 * M);
-  const size_t need = o_sites + noalloc_a256(site_bytes);
-  if (need > kNoAllocScratchBytes)
-    return fail(GMPS_ERR_CAPACITY, "instance needs " + std::to_string(need) +
-                                       " bytes of static scratch; grover_mps_run_noalloc holds " +
-                                       std::to_string(kNoAllocScratchBytes));
-  const int smax = max_smem_optin();
-  SmemPlan sp = make_plan(n, M, xcap, chicap, sizeof(double), site_bytes);
-  int resident = 1;
-  if (sp.total > (size_t)smax) {
-    resident = 0;
-    sp = make_plan(n, M, xcap, chicap, sizeof(double), 0);
-    if (sp.total > (size_t)smax) return fail(GMPS_ERR_UNSUPPORTED, "working set exceeds shared memory");
-  }
-  const int threads = xcap <= 16 ? 64 : (xcap <= 32 ? 128 : 256);
-
-  void* base = nullptr;
-  cudaError_t e = noalloc_scratch_address(&base);
-  if (e != cudaSuccess) return fail(GMPS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-  unsigned char* b = (unsigned char*)base;
-  InstDesc d{};
-  d.n = n;
-  d.M = M;
-  d.apply = apply;
-  d.chi_max = chi_max;
-  d.chicap = chicap;
-  d.xcap = xcap;
-  d.max_sweeps = kDefaultMaxSweeps;
-  d.resident = resident;
-  d.k = k;
-  d.phase_offset = 0;
-  d.tol = tol;
-  d.trunc_eps = 2.220446049250313e-16;
-  d.inv_sqrt_N = ldexp(1.0, -n / 2) * ((n & 1) ? sqrt(0.5) : 1.0);
-  d.marked = (const unsigned long long*)(b + o_marked);
-  d.phi = dev_phi;
-  d.psi = dev_psi;
-  d.sites = b + o_sites;
-  d.site_off = (const long long*)(b + o_off);
-  d.stats = (DevStats*)(b + o_stats);
-  const InstDesc* d_desc = (const InstDesc*)(b + o_desc);
-  double* d_amp = (double*)(b + o_amp);
-#define NA_TRY(x)                                                                          \
-  do {                                                                                     \
-    cudaError_t e_ = (x);                                                                  \
-    if (e_ != cudaSuccess) return fail(GMPS_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
-  } while (0)
-  // everything the kernels read is rewritten here: the array keeps the
-  // previous call's contents
-  NA_TRY(cudaMemcpyAsync(b + o_desc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, stream));
-  NA_TRY(cudaMemcpyAsync(b + o_off, off, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, stream));
-  NA_TRY(cudaMemcpyAsync(b + o_marked, marked, sizeof(uint64_t) * M, cudaMemcpyHostToDevice, stream));
-  NA_TRY(launch_init(d_desc, 1, GMPS_C128, 64, stream));  // statistics and the |+>^n chain
-  if (k > 0) NA_TRY(launch_iterate(d_desc, 1, nullptr, GMPS_C128, threads, sp.total, 1, stream));
-  NA_TRY(launch_amplitudes(d_desc, 0, GMPS_C128, (const unsigned long long*)(b + o_marked), M, d_amp, stream));
-  double amps[2 * kMaxMarked];
-  int status = 0;
-  NA_TRY(cudaMemcpyAsync(amps, d_amp, sizeof(double) * 2 * M, cudaMemcpyDeviceToHost, stream));
-  NA_TRY(cudaMemcpyAsync(&status, b + o_stats + offsetof(DevStats, status), sizeof(int), cudaMemcpyDeviceToHost,
-                         stream));
-  NA_TRY(cudaStreamSynchronize(stream));
-#undef NA_TRY
-  if (status != 0) return fail((gmps_status)status, "device reported an error (status " + std::to_string(status) + ")");
-  double p = 0.0;
-  for (int i = 0; i < M; ++i) p += amps[2 * i] * amps[2 * i] + amps[2 * i + 1] * amps[2 * i + 1];
-  *p_marked = p;
-  if (amp_marked)
-    for (int i = 0; i < 2 * M; ++i) amp_marked[i] = amps[i];
-  return GMPS_OK;
-}
-
-#ifdef GMPS_PROF
-// per-phase cycle counters of the profiling build (read and cleared)
-extern "C" int gmps_prof_read(unsigned long long* out) {
-  cudaDeviceSynchronize();
-  if (cudaMemcpyFromSymbol(out, gmps::g_prof, sizeof(unsigned long long) * 16) != cudaSuccess) return 1;
-  unsigned long long z[16] = {0};
-  return cudaMemcpyToSymbol(gmps::g_prof, z, sizeof(z)) != cudaSuccess;
-}
-#endif

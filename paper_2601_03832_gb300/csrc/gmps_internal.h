@@ -30,6 +30,8 @@ struct DevStats {
   double log_norm;
   double discarded;
   int chi[kMaxN + 1];       // bond table after the last sweep pair
+  unsigned long long t_begin, t_end;  // device clock (ns) when the last launch began and ended this instance
+  int sm;                   // SM that ran it
 };
 
 // Everything one persistent block needs for one instance.  Lives in device
@@ -46,7 +48,8 @@ struct InstDesc {
   long long k;              // iterations to apply in this launch
   long long phase_offset;   // index of this launch's first phase in phi/psi
   double tol;
-  double trunc_eps;         // eps of the storage type for the rank rule
+  double trunc_eps;         // eps of the rank rule (see trunc_dim)
+  int trunc_dim;            // 1: the rank floor is max(m, n) * trunc_eps; 0: trunc_eps itself
   double inv_sqrt_N;        // 2^{-n/2}
   const unsigned long long* marked;  // device, M strings
   const double* phi;        // device, or null = pi
@@ -56,6 +59,16 @@ struct InstDesc {
   DevStats* stats;          // device
   double* rec;              // optional: before each iteration, the marked amplitudes and
                             // <s|psi> of the chain, (M+1) complex per iteration
+};
+
+// Per-chain arguments of the adjoint kernel (one entry per costate chain).
+struct AdjArgs {
+  const double* rec;   // forward chain's marked amplitudes and <s|psi> of the segment
+  const double* phi;   // all K phases of the chain's phase vector
+  const double* psi;
+  double* gphi;        // K gradient entries each
+  double* gpsi;
+  double scale;        // dL/dP
 };
 
 // Shared-memory plan of one block (bytes), identical on host and device.
@@ -130,11 +143,10 @@ cudaError_t launch_amplitudes(const InstDesc* d_desc, int inst, int dtype,
 cudaError_t launch_sample(const InstDesc* d_desc, int inst, int dtype, int chmax, long long shots,
                           unsigned long long seed, unsigned long long* d_bits,
                           double* d_margin, cudaStream_t stream);
-cudaError_t launch_copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int dtype,
+cudaError_t launch_copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int count, int dtype,
                               cudaStream_t stream);
-cudaError_t launch_adjoint(const InstDesc* d_mu, int dtype, int threads, size_t smem, const double* rec,
-                           long long k_lo, long long k_hi, const double* phi, const double* psi, double scale,
-                           double* gphi, double* gpsi, int project, cudaStream_t stream);
+cudaError_t launch_adjoint(const InstDesc* d_mu, const AdjArgs* d_args, int count, int dtype, int threads,
+                           size_t smem, long long k_lo, long long k_hi, int project, cudaStream_t stream);
 cudaError_t launch_batch_prob(const InstDesc* d_desc, int count, int dtype, double* d_p,
                               cudaStream_t stream);
 size_t storage_bytes(int dtype);      // bytes of one complex site element

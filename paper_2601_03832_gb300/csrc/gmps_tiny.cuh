@@ -24,21 +24,6 @@
 // helpers.
 #pragma once
 
-#ifdef GMPS_PROF
-#define TPROF_T0 long long _tp = clock64();
-#define TPROF_MARK(i)                                         \
-  do {                                                        \
-    __syncwarp();                                             \
-    if ((threadIdx.x & 31) == 0 && blockIdx.x == 0) {         \
-      long long _n = clock64();                               \
-      atomicAdd(&g_prof[i], (unsigned long long)(_n - _tp));  \
-      _tp = _n;                                               \
-    }                                                         \
-  } while (0)
-#else
-#define TPROF_T0
-#define TPROF_MARK(i)
-#endif
 
 template <class T>
 __device__ __forceinline__ cx<T> shcx(cx<T> v, int src) {
@@ -116,7 +101,6 @@ __device__ int tiny_qr_factor(cx<T> w0, int m, int n, T floor_rel2, cx<T>* Rp, c
   const int pmax = min(m, n);
   int rank = pmax;
   T flr = 0;
-  TPROF_T0
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (j >= pmax) break;
@@ -150,7 +134,6 @@ __device__ int tiny_qr_factor(cx<T> w0, int m, int n, T floor_rel2, cx<T>* Rp, c
         pc = pj;
       }
     }
-    TPROF_MARK(2);
     const bool colj = c == j && i >= j && i < m;
     // reflector from the pivot column (scaled by a power of two first when the
     // arithmetic has FP32's exponent range)
@@ -196,7 +179,6 @@ __device__ int tiny_qr_factor(cx<T> w0, int m, int n, T floor_rel2, cx<T>* Rp, c
     if (j == 1) be1 = b;
     if (j == 2) be2 = b;
     if (j == 3) be3 = b;
-    TPROF_MARK(3);
     // columns right of j: x <- x - v (v^dag x)
     const cx<T> vi = shcx(a, j * 8 + i);
     const bool upd = live && c > j && i >= j;
@@ -205,9 +187,7 @@ __device__ int tiny_qr_factor(cx<T> w0, int m, int n, T floor_rel2, cx<T>* Rp, c
     const int g0 = lane & ~7;
     const cx<T> d = mk<T>(shidx(t, g0), shidx(t, g0 + 4));
     if (upd) a = cmac(a, vi, mk<T>(-d.re, -d.im));
-    TPROF_MARK(4);
   }
-  TPROF_MARK(2);
   const int p = rank;
   // R P^T: row i < p; the column at position c is original column pc
   if (live && i < p) Rp[i * n + pc] = c > i ? a : (c == i ? pick4(be0, be1, be2, be3, i) : zero);
@@ -224,7 +204,6 @@ __device__ void tiny_q_store(cx<T> a, int m, int p, S* dst) {
   const int lane = threadIdx.x & 31;
   const int c = lane >> 3, i = lane & 7;
   const cx<T> zero = mk<T>(0, 0);
-  TPROF_T0
   cx<T> q;
   {
     const cx<T> vl = shcx(a, (p - 1) * 8 + i), vc = shcx(a, (p - 1) * 8 + c);
@@ -244,7 +223,6 @@ __device__ void tiny_q_store(cx<T> a, int m, int p, S* dst) {
     if (in) q = cmac(q, vj, mk<T>(-d.re, -d.im));
   }
   if (c < p && i < m) st(dst + i * p + c, q);
-  TPROF_MARK(5);
 }
 
 // Hand-off of a small QR step between warps: two buffers (by site parity),
@@ -273,7 +251,6 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
   const bool inU = row && j >= c && j < c + rl;
   const cx<T> zero = mk<T>(0, 0);
   S* A = B.slot(l);
-  TPROF_T0
   cx<T> x = zero;
   if (inM) {
     const int s = j >= kr ? 1 : 0, jj = j - s * kr;
@@ -292,10 +269,8 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
   } else {
     frob = B.tmisc[9];
   }
-  const T eps_rule = B.tmisc[0];
-  const T fl = (T)max(rl, c) * eps_rule * (T)0.25f;
+  const T fl = rank_floor(B, rl, c) * (T)0.25f;
   const T skip2 = frob * fl * fl;
-  TPROF_MARK(6);
   // Jacobi sweeps; the round-robin rounds pair row p with p ^ dx.  own2 keeps
   // this row's |x_p|^2 from the latest round (sigma_p^2 once a sweep ends
   // without rotating)
@@ -350,7 +325,6 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
       }
     }
   }
-  TPROF_MARK(8);
   // sigma_p^2 (rows are orthogonal): the last sweep's Gram diagonal when it
   // rotated nothing, else summed afresh; ranks, rank rule
   const T sp = sw > 0 ? (row ? own2 : (T)0) : sum8(inM ? abs2(x) : (T)0);
@@ -376,7 +350,7 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
     perm[t] = who;
   }
   const T smax = pick4(s0, s1, s2, s3, perm[0]);
-  const T fr = fmax(B.tmisc[1], (T)max(rl, c) * eps_rule);
+  const T fr = fmax(B.tmisc[1], rank_floor(B, rl, c));
   const T thr2 = fr * fr * smax;
   int k = 0;
 #pragma unroll
@@ -419,5 +393,4 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
       B.US[(j - c) * k + myrank] = mk<T>(x.re * sg, -(x.im * sg));
     }
   }
-  TPROF_MARK(9);
 }

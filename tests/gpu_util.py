@@ -15,3 +15,15 @@ def right_orthonormal_error(A):
     cl, _, cr = A.shape
     m = A.reshape(cl, 2 * cr)
     return float(np.abs(m @ m.conj().T - np.eye(cl)).max())
+
+
+def schmidt_from_sites(sites, cut):
+    """Schmidt values across `cut` (sites < cut | sites >= cut) of a
+    right-canonical chain (sites 1..n-1 right-orthonormal, as the SVD sweep
+    leaves it): the singular values of the left block's R factor,
+    accumulated by QR from the left."""
+    R = np.ones((1, 1), dtype=np.complex128)
+    for A in sites[:cut]:
+        B = np.einsum("ij,jsk->isk", R, A)
+        _, R = np.linalg.qr(B.reshape(-1, B.shape[2]))
+    return np.linalg.svd(R, compute_uv=False)

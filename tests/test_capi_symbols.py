@@ -7,14 +7,15 @@ import re
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "grover_mps.h")).read()
-    return sorted(set(re.findall(r"\b(grover_mps_\w+)\s*\(", src)))
+def _declared(header="grover_mps.h", prefix="grover_mps_"):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    return sorted(set(re.findall(r"\b(" + prefix + r"\w+)\s*\(", src)))
 
 
 def test_header_and_binding_agree():
     from paper_2601_03832_gb300 import binding
     assert sorted(binding.EXPORTS) == _declared()
+    assert sorted(binding.SV_EXPORTS) == _declared("grover_sv.h", "grover_sv_")
 
 
 def test_library_exports_every_declared_symbol():
@@ -22,8 +23,12 @@ def test_library_exports_every_declared_symbol():
     __graft_entry__.build()
     from paper_2601_03832_gb300 import binding
     lib = ctypes.CDLL(binding.LIB_PATH)
-    missing = [s for s in _declared() if not hasattr(lib, s)]
+    declared = _declared() + _declared("grover_sv.h", "grover_sv_")
+    missing = [s for s in declared if not hasattr(lib, s)]
     assert not missing, missing
+    from paper_2601_03832_gb300 import peaks
+    plib = ctypes.CDLL(peaks.LIB_PATH)
+    assert all(hasattr(plib, s) for s in _declared("gmps_peaks.h", "gmps_peak_"))
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
@@ -67,4 +72,51 @@ def test_config_validation_needs_no_gpu():
         with pytest.raises(B.GMPSError) as e:
             B.GroverMPS(n, marked, **kw)
         assert e.value.status == status, (n, marked, kw)
+        assert text in str(e.value), (str(e.value), text)
+
+
+def test_noalloc_validation_matches_handle_path_without_gpu():
+    """grover_mps_run_noalloc validates with the same routine as
+    grover_mps_create_ex (same statuses and messages), before any CUDA call."""
+    import pytest
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_03832_gb300 import binding as B
+    cases = [
+        (dict(n=0, marked=[0]), 1, "n must be"),
+        (dict(n=20, marked=list(range(65))), 9, "built maximum"),
+        (dict(n=5, marked=[3, 3]), 1, "duplicate"),
+        (dict(n=5, marked=[40]), 1, "bits >= n"),
+        (dict(n=5, marked=[3], chi_max=0), 1, "chi_max"),
+        (dict(n=5, marked=[3], tol=float("nan")), 1, "tol"),
+        (dict(n=5, marked=[3], apply=3), 1, "apply"),
+        (dict(n=5, marked=[3], k=-1), 1, "k must be"),
+    ]
+    for kw, status, text in cases:
+        n, marked, k = kw.pop("n"), kw.pop("marked"), kw.pop("k", 1)
+        with pytest.raises(B.GMPSError) as e:
+            B.run_noalloc(n, marked, k, **kw)
+        assert e.value.status == status, (n, marked, kw)
+        assert text in str(e.value), (str(e.value), text)
+
+
+def test_statevector_validation_needs_no_gpu():
+    """grover_sv_create refuses invalid arguments before any CUDA call."""
+    import pytest
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_03832_gb300 import binding as B
+    cases = [
+        (dict(n=0, marked=[0]), "n must be"),
+        (dict(n=37, marked=[0]), "n must be"),
+        (dict(n=5, marked=[]), "M must be"),
+        (dict(n=1, marked=[0, 1]), "M must be < 2^n"),
+        (dict(n=5, marked=[3, 3]), "duplicate"),
+        (dict(n=5, marked=[40]), "bits >= n"),
+        (dict(n=5, marked=[3], dtype="dw"), "dtype"),
+    ]
+    for kw, text in cases:
+        with pytest.raises(B.GMPSError) as e:
+            B.GroverSV(**kw)
+        assert e.value.status == 1
         assert text in str(e.value), (str(e.value), text)

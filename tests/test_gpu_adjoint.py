@@ -100,20 +100,21 @@ def test_backward_requires_differentiable_handle(B):
     assert e.value.status == 7
 
 
-def test_concurrent_batch_matches_one_by_one(B):
-    """loss_and_grad_batch runs the phase vectors side by side (one handle,
-    stream and host thread each); every vector's loss and gradients equal
-    those of the same handle run alone, and the reduced model's."""
+@pytest.mark.parametrize("apply,every", [("fused", 8), ("split", 5), ("mpo", 16)])
+def test_batched_launch_matches_one_by_one(B, apply, every):
+    """grover_mps_diff_batch_run runs the phase vectors as batched launches;
+    every vector's loss and gradients equal those of a differentiable handle
+    run alone (same kernels, same arithmetic), and the reduced model's."""
     import torch
     from paper_2601_03832_gb300 import autograd as AG
     n, M, K = 12, 3, 16
     marked = inputs.marked_strings(n, M, seed=91)
     rng = np.random.default_rng(5)
     phis, psis = rng.normal(np.pi, 0.3, (6, K)), rng.normal(np.pi, 0.3, (6, K))
-    L, gphi, gpsi = AG.loss_and_grad_batch(n, marked, phis, psis)
+    L, gphi, gpsi = AG.loss_and_grad_batch(n, marked, phis, psis, apply=apply, checkpoint_every=every)
     torch.cuda.synchronize()
     for b in range(len(phis)):
-        h = AG.differentiable_handle(n, marked, K)
+        h = AG.differentiable_handle(n, marked, K, apply=apply, checkpoint_every=every)
         h.iterate(K, phis[b], psis[b])
         l1 = 1.0 - h.prob_marked()
         g1, g2 = h.backward(-1.0)
@@ -121,5 +122,18 @@ def test_concurrent_batch_matches_one_by_one(B):
         assert abs(L[b] - l1) < 1e-14
         assert np.abs(gphi[b] - g1).max() < 1e-14 and np.abs(gpsi[b] - g2).max() < 1e-14
         Lr, rphi, rpsi = reduced.loss_and_grad(n, M, phis[b], psis[b])
+        assert abs(L[b] - Lr) < 1e-10
+        assert np.abs(gphi[b] - rphi).max() < TOL_G and np.abs(gpsi[b] - rpsi).max() < TOL_G
+
+
+def test_differentiable_batch_of_64_against_reduced_model(B):
+    """The differentiable workload (n = 20, M = 4, K = 64, 64 phase vectors
+    N(pi, 0.1) in float32, checkpoint every 8) in one batched run: every loss
+    and gradient entry against the invariant-plane reverse mode."""
+    from paper_2601_03832_gb300 import autograd as AG
+    inst, phi, psi = inputs.config_differentiable(B=64)
+    L, gphi, gpsi = AG.loss_and_grad_batch(inst.n, inst.marked, phi, psi)
+    for b in range(64):
+        Lr, rphi, rpsi = reduced.loss_and_grad(inst.n, inst.M, phi[b], psi[b])
         assert abs(L[b] - Lr) < 1e-10
         assert np.abs(gphi[b] - rphi).max() < TOL_G and np.abs(gpsi[b] - rpsi).max() < TOL_G

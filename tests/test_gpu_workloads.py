@@ -1,0 +1,185 @@
+"""The configured workloads at their full sizes, through the C ABI, against
+the CPU oracle, the closed form (Sec. II, Eqs. 5-6) and the exact Schmidt
+spectrum.
+
+  * n = 29, M = 1, k = 18198 in FP64 against the FP64 MPS oracle run to the
+    same k (marked probability, amplitude, bonds, 4096 + 1 shots bit-exact
+    off ties);
+  * the complex64 precision form (FP32 storage and contraction, FP64 QR/SVD
+    and bookkeeping) on the same instance and on the 31 instances of the
+    512-instance batched workload with n >= 30 and M >= 14 (full k_i = 4000),
+    each within the stated complex64 bounds, with exact bond tables and a
+    binomial test of the sampled marked count;
+  * n = 40, M = 32, tol = 1e-12 (the multi-marked workload, fused contraction
+    of expanded bond chi + M + 1 = 66) for a short k, against the closed form
+    and the exact Schmidt values at several cuts;
+  * the complex64 sampler and the complex64 form with general phases.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mps as omps
+from oracle import reduced
+from oracle import statevector as sv
+from paper_2601_03832_gb300 import inputs
+from tests.gpu_util import dense_from_sites, schmidt_from_sites
+
+pytestmark = pytest.mark.gpu
+
+TOL_P_F64 = 1e-10            # FP64 marked probability (absolute)
+TOL_AMP_F64 = 1e-10          # FP64 marked amplitude at full k (absolute)
+# complex64 precision form, stated bounds (absolute) at the configured sizes:
+# marked probability and marked amplitude against the closed form
+TOL_P_C64_FULL = 1e-4
+TOL_AMP_C64_FULL = 1e-4
+# FP64 marked amplitude at n = 40 (|a_w| ~ 7e-6 after 3 iterations): absolute
+TOL_AMP_N40 = 1e-12
+# complex64 rank floor of the C API (fixed 2^-22 sigma_0)
+RANK_FLOOR_C64 = 2.0 ** -22
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_03832_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _binomial_ok(count, shots, p, z=6.0):
+    return abs(count - shots * p) <= z * math.sqrt(shots * p * (1 - p)) + 1
+
+
+def test_headline_n29_fp64_against_oracle(B):
+    inst = inputs.config_n29()
+    g = B.GroverMPS(inst.n, inst.marked, dtype="c128", apply="fused", chi_max=inst.chi_max)
+    g.iterate(inst.k)
+    ref = omps.grover_iterate(omps.plus_state(inst.n), inst.marked, inst.k, inst.chi_max, mode="fused")
+    P_or = omps.prob_marked(ref, inst.marked)
+    P_cf = reduced.closed_form(inst.n, 1, inst.k)[0]
+    P = g.prob_marked()
+    assert abs(P - P_or) <= TOL_P_F64 and abs(P - P_cf) <= TOL_P_F64
+    a = g.amplitude(inst.marked[0])
+    assert abs(a - omps.amplitude(ref, inst.marked[0])) <= TOL_AMP_F64
+    assert g.stats()["chi"] == ref.bonds() == [1] + [2] * (inst.n - 1) + [1]
+    for shots in (4096, 1):
+        bits = g.sample(shots, 2)
+        obits, margin = omps.sample(ref, shots, 2)
+        ok = margin > 1e-12
+        assert ok.sum() >= shots - 1
+        assert np.array_equal(bits[ok], obits[ok])
+    g.close()
+
+
+def test_c64_n29_full_k_within_stated_bound(B):
+    inst = inputs.config_n29()
+    g = B.GroverMPS(inst.n, inst.marked, dtype="c64", apply="fused", chi_max=inst.chi_max)
+    g.iterate(inst.k)
+    P_cf, aw, _ = reduced.closed_form(inst.n, 1, inst.k)
+    P = g.prob_marked()
+    assert abs(P - P_cf) <= TOL_P_C64_FULL, P - P_cf
+    a = g.amplitude(inst.marked[0])
+    assert abs(a - aw) <= TOL_AMP_C64_FULL
+    st = g.stats()
+    assert st["chi"] == [1] + [2] * (inst.n - 1) + [1]
+    bits = g.sample(4096, 2)
+    assert _binomial_ok(int(np.sum(bits == inst.marked[0])), 4096, P_cf)
+    g.close()
+
+
+def test_c64_batched_worst_instances_full_k(B):
+    """The batched workload's instances with n >= 30 and M >= 14 (where the
+    marked component's Schmidt values are smallest), complex64, full k_i, in
+    one persistent launch: P and the marked amplitudes within the stated
+    bounds, every bond equal to the exact Schmidt rank."""
+    allb = inputs.config_batched(count=512)
+    insts = [x for x in allb if x.n >= 30 and x.M >= 14]
+    assert len(insts) == 31
+    b = B.GroverBatch(insts, dtype="c64", apply="fused")
+    b.run(use_graph=False)
+    p, st, rc = b.result()
+    assert rc == 0 and not st.any()
+    for i, x in enumerate(insts):
+        P_cf, aw, _ = reduced.closed_form(x.n, x.M, x.k)
+        assert abs(p[i] - P_cf) <= TOL_P_C64_FULL, (x.tag, p[i] - P_cf)
+        for w in x.marked[:2]:
+            assert abs(b.amplitude(i, w) - aw) <= TOL_AMP_C64_FULL, x.tag
+        chi = b.stats(i)["chi"]
+        for cut in range(1, x.n):
+            assert chi[cut] == reduced.exact_bond(x.n, x.marked, x.k, cut), (x.tag, cut)
+    b.close()
+
+
+def test_multi_marked_n40_short_k_schmidt_spectrum(B):
+    """n = 40, M = 32, chi_max = 128, tol = 1e-12, fused (expanded bond 66,
+    256 threads, chain outside shared memory) for k = 3: P against the closed
+    form (relative), amplitudes, and the Schmidt values of the exported chain
+    against the exact spectrum at several cuts."""
+    k = 3
+    mi = inputs.config_multi_marked(k=k)
+    g = B.GroverMPS(mi.n, mi.marked, dtype="c128", apply="fused", chi_max=mi.chi_max, tol=mi.tol)
+    g.iterate(k)
+    P_cf, aw, _ = reduced.closed_form(mi.n, mi.M, k)
+    P = g.prob_marked()
+    assert abs(P - P_cf) <= 1e-9 * P_cf
+    for w in mi.marked[:4]:
+        assert abs(g.amplitude(w) - aw) <= TOL_AMP_N40
+    st = g.stats()
+    sites = g.export()
+    for cut in (1, 5, 10, 20, 30, 39):
+        ex = reduced.schmidt_values(mi.n, mi.marked, k, cut)
+        kept = ex[ex > mi.tol * ex[0]]
+        assert st["chi"][cut] == len(kept), cut
+        got = schmidt_from_sites(sites, cut)
+        assert np.abs(got[: len(kept)] - kept).max() <= 1e-9 * kept[0], cut
+    g.close()
+
+
+def test_c64_sampler_agrees_with_oracle_off_near_ties(B):
+    """complex64 sampler (FP32 tensors, FP64 probabilities) against the FP64
+    oracle's sampler on the same uniforms: every decision whose oracle margin
+    |u - p0/(p0+p1)| exceeds the complex64 bound is the same."""
+    inst = inputs.config_small()
+    g = B.GroverMPS(inst.n, inst.marked, dtype="c64", apply="fused", chi_max=inst.chi_max)
+    g.iterate(inst.k)
+    ref = omps.grover_iterate(omps.plus_state(inst.n), inst.marked, inst.k, inst.chi_max, mode="fused")
+    for shots, seed in ((4096, 2), (1, 2), (999, 31337)):
+        bits = g.sample(shots, seed)
+        obits, margin = omps.sample(ref, shots, seed)
+        ok = margin > 1e-4
+        assert ok.sum() >= 0.98 * shots
+        assert np.array_equal(bits[ok], obits[ok])
+    # a general state with several marked strings, split contraction
+    n, marked = 9, [3, 300, 77]
+    rng = np.random.default_rng(5)
+    phis, psis = rng.normal(np.pi, 0.5, 4), rng.normal(np.pi, 0.5, 4)
+    g2 = B.GroverMPS(n, marked, dtype="c64", apply="split", chi_max=16)
+    g2.iterate(4, phis, psis)
+    ref2 = omps.grover_iterate(omps.plus_state(n), marked, 4, 16, phis=phis, psis=psis)
+    bits = g2.sample(2000, 99)
+    obits, margin = omps.sample(ref2, 2000, 99)
+    ok = margin > 1e-4
+    assert np.array_equal(bits[ok], obits[ok])
+
+
+TOL_AMP_C64_SMALL = 2e-6
+
+
+@pytest.mark.parametrize("apply", ["mpo", "split", "fused"])
+@pytest.mark.parametrize("n,M", [(3, 2), (7, 3), (9, 4), (11, 2)])
+def test_c64_general_phases_dense(B, apply, n, M):
+    marked = inputs.marked_strings(n, M, seed=200 + 7 * n + M)
+    rng = np.random.default_rng(n * 31 + M)
+    k = 6
+    phis, psis = rng.normal(np.pi, 0.6, k), rng.normal(np.pi, 0.6, k)
+    g = B.GroverMPS(n, marked, dtype="c64", apply=apply, chi_max=64)
+    g.iterate(k, phis, psis)
+    ref = sv.grover(n, marked, k, phis, psis)
+    v = dense_from_sites(g.export())
+    assert np.abs(v - ref).max() < TOL_AMP_C64_SMALL
+    st = g.stats()
+    for cut in range(1, n):
+        assert st["chi"][cut] == reduced.exact_bond(n, marked, k, cut, phis, psis, rtol=RANK_FLOOR_C64)
