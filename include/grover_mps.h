@@ -249,6 +249,41 @@ gmps_status grover_mps_batch_set_threads(gmps_batch_handle b, int threads);
 gmps_status grover_mps_batch_destroy(gmps_batch_handle b);
 
 /* ------------------------------------------------------------------ */
+/* Gate-level circuits (Sec. III-A, Fig. 1A: Common and Iterative).    */
+/* ------------------------------------------------------------------ */
+
+enum {
+  GMPS_GATE_1Q = 0,       /* 2x2 unitary u (row-major, re/im interleaved) on qubit `site` */
+  GMPS_GATE_MCPHASE = 1   /* I - (1 - e^{i u[0]}) |1...1><1...1| on all n qubits (u[0] = pi: the
+                             multi-controlled Z) */
+};
+
+typedef struct gmps_gate {
+  int kind;
+  int site;
+  double u[8];
+} gmps_gate;
+
+/* Apply `count` gates (host array) `repeat` times to the handle's MPS, gate
+ * by gate, in one persistent launch: a one-qubit gate acts on its site
+ * tensor in place (the chain stays canonical); a multi-controlled phase is
+ * contracted as an MPO of bond 2 and recompressed by the QR and truncated
+ * SVD sweeps.  The paper's "Iterative" method passes the gates of one Grover
+ * iteration with repeat = k, its "Common" method the k-iteration circuit with
+ * repeat = 1.  Needs a handle whose expanded bond holds a bond-2 MPO (apply =
+ * GMPS_APPLY_MPO, e.g. grover_mps_create).  Synchronises. */
+gmps_status grover_mps_apply_circuit(gmps_handle h, const gmps_gate* gates, int64_t count, int64_t repeat);
+
+/* The gates of `iterations` Grover iterations as in Fig. 1A: for each marked
+ * string w, X on the qubits where w is 0, the multi-controlled Z, the same
+ * X's (the oracle I - 2|w><w|); then H and X on every qubit, the
+ * multi-controlled Z, X and H on every qubit (the diffusion I - 2|s><s|).
+ * Their product is -G of Sec. II, Eq. 3 (same probabilities).  Writes
+ * *count; with out != NULL also the gates, which need capacity >= *count. */
+gmps_status grover_mps_grover_gates(int n, const uint64_t* marked, int M, int64_t iterations, gmps_gate* out,
+                                    int64_t capacity, int64_t* count);
+
+/* ------------------------------------------------------------------ */
 /* Differentiable batch: many phase vectors of one problem at once.    */
 /* ------------------------------------------------------------------ */
 

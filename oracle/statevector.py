@@ -132,3 +132,19 @@ def adjoint(n: int, marked, phis, psis):
         g_psi[k - 1] = -2.0 * np.real(-1j * e_psi * np.vdot(mu, s) * np.vdot(s, o_prev))
         mu = apply_oracle(nu, marked, np.conj(e_phi))      # O^dag = I - (1 - e^{-i phi}) Pi_W
     return 1.0 - P, g_phi, g_psi
+
+
+# --------------------------------------------------------- gate-level circuits
+def apply_1q(v: np.ndarray, n: int, site: int, u: np.ndarray) -> np.ndarray:
+    """A one-qubit gate u (2 x 2) on qubit `site` (bit `site` of the index), the
+    elementary gates H and X of the circuit in Fig. 1A."""
+    t = v.reshape(1 << (n - 1 - site), 2, 1 << site)
+    return np.einsum("st,atb->asb", np.asarray(u, dtype=np.complex128), t).reshape(-1)
+
+
+def apply_mcphase(v: np.ndarray, phase: float) -> np.ndarray:
+    """I - (1 - e^{i phase}) |1...1><1...1|: the multi-controlled phase of
+    Fig. 1A (phase pi: the multi-controlled Z)."""
+    out = v.copy()
+    out[-1] *= complex(np.cos(phase), np.sin(phase))
+    return out

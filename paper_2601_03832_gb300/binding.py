@@ -32,7 +32,8 @@ EXPORTS = [
     "grover_mps_batch_amplitude", "grover_mps_batch_stats", "grover_mps_batch_set_threads",
     "grover_mps_batch_destroy",
     "grover_mps_launch_count", "grover_mps_run_noalloc", "grover_mps_diff_batch_create",
-    "grover_mps_diff_batch_run", "grover_mps_diff_batch_destroy",
+    "grover_mps_diff_batch_run", "grover_mps_diff_batch_destroy", "grover_mps_apply_circuit",
+    "grover_mps_grover_gates",
 ]
 # every symbol include/grover_sv.h declares
 SV_EXPORTS = [
@@ -46,6 +47,13 @@ class gmps_config(C.Structure):
                 ("apply", C.c_int), ("chi_max", C.c_int), ("tol", C.c_double), ("max_sweeps", C.c_int),
                 ("threads", C.c_int), ("differentiable", C.c_int), ("checkpoint_every", C.c_int),
                 ("max_iters", C.c_int), ("arena", C.c_void_p), ("arena_bytes", C.c_size_t)]
+
+
+class gmps_gate(C.Structure):
+    _fields_ = [("kind", C.c_int), ("site", C.c_int), ("u", C.c_double * 8)]
+
+
+GATE_1Q, GATE_MCPHASE = 0, 1
 
 
 class gmps_stats(C.Structure):
@@ -107,6 +115,8 @@ def load():
         "grover_mps_batch_set_threads": [vp, i32],
         "grover_mps_batch_destroy": [vp],
         "grover_mps_run_noalloc": [i32, P(u64), i32, i32, i32, f64, i64, vp, vp, vp, P(f64), P(f64), P(i32)],
+        "grover_mps_apply_circuit": [vp, P(gmps_gate), i64, i64],
+        "grover_mps_grover_gates": [i32, P(u64), i32, i64, P(gmps_gate), i64, P(i64)],
         "grover_mps_diff_batch_create": [P(gmps_config), i32, i32, vp, P(vp)],
         "grover_mps_diff_batch_run": [vp, P(f64), P(f64), P(f64), P(f64), P(f64)],
         "grover_mps_diff_batch_destroy": [vp],
@@ -233,6 +243,10 @@ class GroverMPS:
         _check(load().grover_mps_stats(self.h, C.byref(s)))
         return _stats_dict(s, self.n)
 
+    def apply_circuit(self, gates, repeat=1):
+        """Apply a gate array (from grover_gates or make_gates) `repeat` times."""
+        _check(load().grover_mps_apply_circuit(self.h, gates, len(gates), int(repeat)))
+
     def export(self):
         """Site tensors as a list of complex128 arrays (chi_l, 2, chi_{l+1})."""
         lib = load()
@@ -259,6 +273,32 @@ class GroverMPS:
             self.close()
         except Exception:
             pass
+
+
+def grover_gates(n, marked, iterations=1):
+    """The gates of `iterations` Grover iterations (grover_mps_grover_gates)."""
+    lib = load()
+    m = np.ascontiguousarray(np.asarray(marked, dtype=np.uint64))
+    cnt = C.c_int64()
+    mp = m.ctypes.data_as(C.POINTER(C.c_uint64))
+    _check(lib.grover_mps_grover_gates(int(n), mp, len(m), int(iterations), None, 0, C.byref(cnt)))
+    arr = (gmps_gate * cnt.value)()
+    _check(lib.grover_mps_grover_gates(int(n), mp, len(m), int(iterations), arr, cnt.value, C.byref(cnt)))
+    return arr
+
+
+def make_gates(ops):
+    """Gate array from (kind, site, 2x2 complex matrix or phase) tuples."""
+    arr = (gmps_gate * len(ops))()
+    for g, (kind, site, val) in zip(arr, ops):
+        g.kind, g.site = kind, site
+        if kind == GATE_1Q:
+            u = np.asarray(val, dtype=np.complex128).reshape(4)
+            for q in range(4):
+                g.u[2 * q], g.u[2 * q + 1] = u[q].real, u[q].imag
+        else:
+            g.u[0] = float(val)
+    return arr
 
 
 def run_noalloc(n, marked, k, apply="mpo", chi_max=4, tol=0.0, dev_phi=0, dev_psi=0, stream=None):

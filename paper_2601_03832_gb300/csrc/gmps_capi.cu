@@ -178,6 +178,10 @@ struct gmps_ctx {
   unsigned long long* d_marked = nullptr;
   unsigned long long* d_qbits = nullptr;  // M+1 query strings
   double* d_qout = nullptr;               // 2(M+1)
+  InstDesc* d_cdesc = nullptr;            // gate-level circuits: the chain with the all-ones string
+  unsigned long long* d_ones = nullptr;
+  GateOp* d_gates = nullptr;
+  size_t gate_cap = 0;
   double* d_phase = nullptr;
   size_t phase_cap = 0;
   unsigned long long* d_sample = nullptr;
@@ -219,7 +223,8 @@ static char* carve_slab(char* p, const gmps_config* c, const Plan& P, Slab* s) {
 
 static size_t arena_size(const gmps_config* c, const Plan& P) {
   return slab_bytes(c, P) + a256(sizeof(unsigned long long) * c->M) +
-         a256(sizeof(unsigned long long) * (c->M + 1)) + a256(sizeof(double) * 2 * (c->M + 1));
+         a256(sizeof(unsigned long long) * (c->M + 1)) + a256(sizeof(double) * 2 * (c->M + 1)) +
+         a256(sizeof(InstDesc)) + a256(sizeof(unsigned long long));
 }
 
 static InstDesc base_desc(const gmps_ctx* h, const Slab& s) {
@@ -323,6 +328,10 @@ gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps
   h->d_qbits = (unsigned long long*)p;
   p += a256(sizeof(unsigned long long) * (cfg->M + 1));
   h->d_qout = (double*)p;
+  p += a256(sizeof(double) * 2 * (cfg->M + 1));
+  h->d_cdesc = (InstDesc*)p;
+  p += a256(sizeof(InstDesc));
+  h->d_ones = (unsigned long long*)p;
   cudaError_t e = cudaMemcpyAsync(h->d_marked, h->marked.data(), sizeof(uint64_t) * cfg->M,
                                   cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) {
@@ -669,6 +678,95 @@ gmps_status grover_mps_backward(gmps_handle h, double dL_dP, double* grad_phi, d
   return s;
 }
 
+static_assert(sizeof(gmps_gate) == sizeof(GateOp), "gmps_gate and GateOp must share their layout");
+
+gmps_status grover_mps_apply_circuit(gmps_handle h, const gmps_gate* gates, int64_t count, int64_t repeat) {
+  if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
+  if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
+  if (count < 0 || repeat < 0) return fail(GMPS_ERR_ARG, "count and repeat must be >= 0");
+  if (count == 0 || repeat == 0) return GMPS_OK;
+  if (!gates) return fail(GMPS_ERR_ARG, "gates is NULL");
+  if (h->cfg.differentiable) return fail(GMPS_ERR_UNSUPPORTED, "circuits on differentiable handles are not built");
+  if (h->plan.xcap < 2 * h->plan.chicap)
+    return fail(GMPS_ERR_UNSUPPORTED, "circuits need a handle created with apply = GMPS_APPLY_MPO");
+  for (int64_t g = 0; g < count; ++g) {
+    const gmps_gate& x = gates[g];
+    if (x.kind == GMPS_GATE_1Q) {
+      if (x.site < 0 || x.site >= h->cfg.n) return fail(GMPS_ERR_ARG, "gate site out of range");
+    } else if (x.kind != GMPS_GATE_MCPHASE) {
+      return fail(GMPS_ERR_ARG, "unknown gate kind");
+    }
+    for (int q = 0; q < 8; ++q)
+      if (!std::isfinite(x.u[q])) return fail(GMPS_ERR_ARG, "non-finite gate entry");
+  }
+  if (h->gate_cap < (size_t)count) {
+    if (h->d_gates) cudaFree(h->d_gates);
+    h->d_gates = nullptr;
+    h->gate_cap = 0;
+    if (cudaMalloc(&h->d_gates, sizeof(GateOp) * count) != cudaSuccess) return fail(GMPS_ERR_OOM, "gate list");
+    h->gate_cap = count;
+  }
+  InstDesc d = base_desc(h, h->main);
+  d.M = 1;
+  d.apply = GMPS_APPLY_MPO;
+  d.marked = h->d_ones;
+  const unsigned long long ones = h->cfg.n == 64 ? ~0ull : ((1ull << h->cfg.n) - 1ull);
+  CUDA_TRY(cudaMemcpyAsync(h->d_ones, &ones, sizeof(ones), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->d_cdesc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->d_gates, gates, sizeof(GateOp) * count, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(launch_circuit(h->d_cdesc, h->d_gates, count, repeat, h->cfg.dtype, h->plan.threads, h->plan.smem,
+                          h->stream));
+  h->all_phases_explicit = false;
+  return check_device(h);
+}
+
+gmps_status grover_mps_grover_gates(int n, const uint64_t* marked, int M, int64_t iterations, gmps_gate* out,
+                                    int64_t capacity, int64_t* count) {
+  if (!count) return fail(GMPS_ERR_ARG, "count is NULL");
+  if (n < 1 || n > 64) return fail(GMPS_ERR_ARG, "n must be in [1, 64]");
+  if (M < 1 || !marked) return fail(GMPS_ERR_ARG, "need M >= 1 marked strings");
+  if (iterations < 0) return fail(GMPS_ERR_ARG, "iterations must be >= 0");
+  int64_t per = 4 * (int64_t)n + 1;  // diffusion
+  for (int i = 0; i < M; ++i) {
+    if (n < 64 && (marked[i] >> n)) return fail(GMPS_ERR_ARG, "marked string has bits >= n");
+    int zeros = 0;
+    for (int l = 0; l < n; ++l) zeros += !((marked[i] >> l) & 1ull);
+    per += 2 * zeros + 1;
+  }
+  *count = per * iterations;
+  if (!out) return GMPS_OK;
+  if (capacity < *count) return fail(GMPS_ERR_ARG, "gate buffer too small");
+  const double r = 0.70710678118654752440;
+  auto one = [](gmps_gate* g, int site, double a, double b, double c, double d) {
+    g->kind = GMPS_GATE_1Q;
+    g->site = site;
+    const double u[8] = {a, 0.0, b, 0.0, c, 0.0, d, 0.0};
+    for (int q = 0; q < 8; ++q) g->u[q] = u[q];
+  };
+  auto mcz = [](gmps_gate* g) {
+    g->kind = GMPS_GATE_MCPHASE;
+    g->site = 0;
+    for (int q = 0; q < 8; ++q) g->u[q] = 0.0;
+    g->u[0] = M_PI;
+  };
+  gmps_gate* g = out;
+  for (int64_t it = 0; it < iterations; ++it) {
+    for (int i = 0; i < M; ++i) {  // oracle of w: X on its zeros, MCZ, X on its zeros
+      for (int l = 0; l < n; ++l)
+        if (!((marked[i] >> l) & 1ull)) one(g++, l, 0, 1, 1, 0);
+      mcz(g++);
+      for (int l = 0; l < n; ++l)
+        if (!((marked[i] >> l) & 1ull)) one(g++, l, 0, 1, 1, 0);
+    }
+    for (int l = 0; l < n; ++l) one(g++, l, r, r, r, -r);  // H
+    for (int l = 0; l < n; ++l) one(g++, l, 0, 1, 1, 0);   // X
+    mcz(g++);
+    for (int l = 0; l < n; ++l) one(g++, l, 0, 1, 1, 0);
+    for (int l = 0; l < n; ++l) one(g++, l, r, r, r, -r);
+  }
+  return GMPS_OK;
+}
+
 gmps_status grover_mps_destroy(gmps_handle h) {
   if (!h) return GMPS_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -677,6 +775,7 @@ gmps_status grover_mps_destroy(gmps_handle h) {
   if (h->d_phase) cudaFree(h->d_phase);
   if (h->d_sample) cudaFree(h->d_sample);
   if (h->diff_mem) cudaFree(h->diff_mem);
+  if (h->d_gates) cudaFree(h->d_gates);
   delete h;
   return GMPS_OK;
 }

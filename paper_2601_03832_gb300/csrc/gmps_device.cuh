@@ -107,6 +107,46 @@ __device__ __forceinline__ void st(dw2* p, cx<dw> v) {
   *p = o;
 }
 __device__ __forceinline__ void st(dw2* p, cx<double> v) { st(p, mk<dw>(dw(v.re), dw(v.im))); }
+
+// Murmur3's 64-bit finaliser (Appleby): a counter-based hash for the
+// stochastic rounding of complex64 stores.
+__device__ __forceinline__ unsigned long long fmix64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+// x rounded to FP32 stochastically: up (away from zero) with probability
+// equal to the dropped fraction of an FP32 unit, using 29 random bits r.
+// Integer operations only (FP64 conversions would occupy the FP64 pipe).
+// Outside FP32's normal range: round to nearest.
+__device__ __forceinline__ float sr_f32(double x, unsigned r) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = b & 0x7fffffffffffffffull;
+  if (mag < 0x3810000000000000ull || mag >= 0x47e0000000000000ull) return (float)x;  // |x| < 2^-126 or >= 2^127
+  b += (unsigned long long)(r >> 3);      // 29 random bits below the FP32 significand
+  b &= ~((1ull << 29) - 1ull);            // truncate: now exactly an FP32 value
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float((hi & 0x80000000u) | ((e - 1023u + 127u) << 23) | m);
+}
+// Store of a site-tensor element: round to nearest, except complex64 storage,
+// which rounds stochastically.  The rounding of FP32 storage repeats nearly
+// the same error every iteration on a slowly changing state, so with round to
+// nearest it adds up linearly over k; stochastic rounding (random bits from
+// the per-store key and the element's index) makes it a random walk.
+template <class V>
+__device__ __forceinline__ void st_site(double2* p, V v, unsigned long long, unsigned) { st(p, v); }
+template <class V>
+__device__ __forceinline__ void st_site(dw2* p, V v, unsigned long long, unsigned) { st(p, v); }
+template <class T>
+__device__ __forceinline__ void st_site(float2* p, cx<T> v, unsigned long long key, unsigned e) {
+  const unsigned long long h = fmix64(key ^ ((unsigned long long)e * 0x9e3779b97f4a7c15ull));
+  *p = make_float2(sr_f32((double)v.re, (unsigned)h), sr_f32((double)v.im, (unsigned)(h >> 32)));
+}
 template <class A, class B>
 __device__ __forceinline__ cx<A> cvt(cx<B> v) { return mk<A>((A)v.re, (A)v.im); }
 template <>
@@ -227,9 +267,14 @@ struct Blk {
   unsigned char* tbuf;     // two buffers: 32 lanes' reflector registers + (p, m) of a small QR step
   int* misc;               // [0] status, [1] max sweeps, [2] sweeps sum, [3] svd count, [4] k kept
   double* dmisc;           // [0] log_norm, [1] discarded, [2..5] phase coefficients
+  unsigned long long rng;  // key of this sweep pair's stochastic rounding (complex64 storage)
   T* tmisc;                // [0] rank-rule eps, [1] tol, [2] discarded weight, [3..6] e^{i phi}-1 and 1-e^{i psi},
                            // [7] 2^{-n/2}, [8] Jacobi skip floor, [9] squared norm of the swept matrices
   __device__ S* slot(int l) const { return sites + off[l]; }
+  // key of the stores into site l in one pass (0: QR sweep, 1: SVD sweep)
+  __device__ unsigned long long key(int l, int pass) const {
+    return fmix64(rng + (((unsigned long long)l << 2) | (unsigned long long)pass));
+  }
 };
 
 // ------------------------------------------------- exponent / scaling helpers
@@ -677,11 +722,17 @@ __device__ __forceinline__ CR mpo_w(int op, int b, int l, int s, int sp, const u
 template <class T, class S, class CR>
 __device__ __forceinline__ cx<T> expand_elem(Blk<T, S>& B, int l, int i, int s, int j, int xl, int mode, int op,
                                              int D, const cx<T>* lbnd, cx<T> cpsi, int nt) {
+  // The chain's own tensors are contracted in CR (the bulk contraction); the
+  // operator's coefficients (MPO boundary, direct-sum product states and
+  // their weights, 1/sqrt 2 of |+>) enter in T: they set every iteration's
+  // rotation, and a CR rounding of them would repeat the same error each
+  // iteration (a drift linear in k for the complex64 form).
   const int n = B.n;
   const int cl = B.chi[l], cr = B.chi[l + 1];
   const S* A = B.slot(l);
-  const CR h = K<CR>::isq2();
-  cx<CR> acc = mk<CR>(0, 0);
+  const T h = K<T>::isq2();
+  cx<CR> acc = mk<CR>(0, 0);  // chain part
+  cx<T> acc_t = mk<T>(0, 0);  // coefficient part
   if (mode == 0) {  // ---- MPO
     if (n == 1) {
       for (int b = 0; b < D; ++b) {
@@ -690,7 +741,7 @@ __device__ __forceinline__ cx<T> expand_elem(Blk<T, S>& B, int l, int i, int s, 
           const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
           if (w != (CR)0) tb = cmac(tb, mk<CR>(w, 0), ld<CR>(A + sp));
         }
-        acc = cmac(acc, cvt<CR>(lbnd[b]), tb);
+        acc_t = cmac(acc_t, lbnd[b], cvt<T>(tb));
       }
     } else if (l == 0) {
       const int b = j / cr, jj = j % cr;
@@ -699,7 +750,7 @@ __device__ __forceinline__ cx<T> expand_elem(Blk<T, S>& B, int l, int i, int s, 
         const CR w = mpo_w<CR>(op, b, l, s, sp, B.d->marked);
         if (w != (CR)0) tb = cmac(tb, mk<CR>(w, 0), ld<CR>(A + sp * cr + jj));
       }
-      acc = cmul(cvt<CR>(lbnd[b]), tb);
+      acc_t = cmul(lbnd[b], cvt<T>(tb));
     } else {
       const bool last = (l == n - 1);
       const int b0 = last ? 0 : j / cr, b1 = last ? D : b0 + 1;
@@ -716,31 +767,33 @@ __device__ __forceinline__ cx<T> expand_elem(Blk<T, S>& B, int l, int i, int s, 
       }
     }
   } else {  // ---- direct sum
-    auto pval = [&](int t) -> CR {
+    auto pval = [&](int t) -> T {
       if (B.tplus[t]) return h;
-      return ((int)((B.tbits[t] >> l) & 1ull) == s) ? (CR)1 : (CR)0;
+      return ((int)((B.tbits[t] >> l) & 1ull) == s) ? (T)1 : (T)0;
     };
     if (n == 1) {
-      acc = cmul(cvt<CR>(cpsi), ld<CR>(A + s));
-      for (int t = 0; t < nt; ++t) acc = cmac(acc, cvt<CR>(B.tcoef[t]), mk<CR>(pval(t), 0));
+      acc_t = cmul(cpsi, ld<T>(A + s));
+      for (int t = 0; t < nt; ++t) acc_t = cmac(acc_t, B.tcoef[t], mk<T>(pval(t), 0));
+      return acc_t;
     } else if (l == 0) {
-      if (j < cr)
-        acc = cmul(cvt<CR>(cpsi), ld<CR>(A + s * cr + j));
-      else
-        acc = cscale(cvt<CR>(B.tcoef[j - cr]), pval(j - cr));
+      if (j < cr) return cmul(cpsi, ld<T>(A + s * cr + j));
+      return cscale(B.tcoef[j - cr], pval(j - cr));
     } else if (l == n - 1) {
       for (int a = 0; a < cl; ++a) acc = cmac(acc, cvt<CR>(B.Rp[i * xl + a]), ld<CR>(A + a * 2 + s));
-      for (int t = 0; t < nt; ++t) acc = cmac(acc, cvt<CR>(B.Rp[i * xl + cl + t]), mk<CR>(pval(t), 0));
+      acc_t = cvt<T>(acc);
+      for (int t = 0; t < nt; ++t) acc_t = cmac(acc_t, B.Rp[i * xl + cl + t], mk<T>(pval(t), 0));
+      return acc_t;
     } else {
       if (j < cr) {
         for (int a = 0; a < cl; ++a)
           acc = cmac(acc, cvt<CR>(B.Rp[i * xl + a]), ld<CR>(A + (a * 2 + s) * cr + j));
-      } else {
-        acc = cscale(cvt<CR>(B.Rp[i * xl + cl + (j - cr)]), pval(j - cr));
+        return cvt<T>(acc);
       }
+      return cscale(B.Rp[i * xl + cl + (j - cr)], pval(j - cr));
     }
   }
-  return cvt<T>(acc);
+  // MPO: the chain part, or at site 0 (and for n = 1) the boundary-weighted part
+  return (n == 1 || l == 0) ? acc_t : cvt<T>(acc);
 }
 template <class T, class S, class CR>
 __device__ void expand_absorb(Blk<T, S>& B, int l, int r, int xl, int xr, int mode, int op, int D,
@@ -813,6 +866,7 @@ template <class T, class S, class CR>
 __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* lbnd, cx<T> cpsi,
                            int nt, int env_nt = 0) {
   const InstDesc& d = *B.d;
+  B.rng = fmix64(B.rng + 0x632be59bd9b4e019ull);  // a fresh rounding key per sweep pair
   const int n = B.n;
   // expanded bond at cut l (0 < l < n)
   auto xb = [&](int l) -> int {
@@ -832,7 +886,8 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
   auto flush_q = [&](int site) {
     if (threadIdx.x >= 32 && threadIdx.x < 64) {
       const int* meta = tbuf_meta<T>(B.tbuf, site & 1);
-      tiny_q_store<T, S>(tbuf_regs<T>(B.tbuf, site & 1)[threadIdx.x & 31], meta[1], meta[0], B.slot(site));
+      tiny_q_store<T, S>(tbuf_regs<T>(B.tbuf, site & 1)[threadIdx.x & 31], meta[1], meta[0], B.slot(site),
+                         B.key(site, 0));
     }
   };
   for (int l = 0; l < n; ++l) {
@@ -860,7 +915,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
             tbuf_meta<T>(B.tbuf, l & 1)[1] = m;
           }
         } else {
-          tiny_q_store<T, S>(a, m, pt, dst);
+          tiny_q_store<T, S>(a, m, pt, dst, B.key(l, 0));
         }
         if (threadIdx.x == 0) B.qb[l + 1] = pt;
       } else if (pend >= 0) {
@@ -878,7 +933,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     }
     expand_absorb<T, S, CR>(B, l, r, xl, xr, mode, op, D, lbnd, cpsi, nt);
     if (l == n - 1) {
-      for (int e = threadIdx.x; e < m; e += blockDim.x) st(dst + e, B.W[e]);
+      for (int e = threadIdx.x; e < m; e += blockDim.x) st_site(dst + e, B.W[e], B.key(l, 0), e);
       if (threadIdx.x == 0) B.qb[n] = 1;
       __syncthreads();
       break;
@@ -896,7 +951,8 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     }
     __syncthreads();
     qr_form_q<T>(B.W, m, p, xr, B.tau);
-    for (int e = threadIdx.x; e < m * p; e += blockDim.x) st(dst + e, B.W[(e / p) * xr + (e % p)]);
+    for (int e = threadIdx.x; e < m * p; e += blockDim.x)
+      st_site(dst + e, B.W[(e / p) * xr + (e % p)], B.key(l, 0), e);
     if (threadIdx.x == 0) B.qb[l + 1] = p;
     __syncthreads();
     r = p;
@@ -916,7 +972,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     }
     __syncthreads();
     const T inv = B.amps[0].re;
-    if (threadIdx.x < 2) st(a + threadIdx.x, cscale(ld<T>(a + threadIdx.x), inv));
+    if (threadIdx.x < 2) st_site(a + threadIdx.x, cscale(ld<T>(a + threadIdx.x), inv), B.key(0, 1), threadIdx.x);
     __syncthreads();
     return;
   }
@@ -1034,7 +1090,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     for (int e = threadIdx.x; e < k * c; e += blockDim.x) {
       const int t = e / c, j = e % c;
       const int pr = B.perm[t];
-      st(dst + e, cscale(B.Mat[pr * c + j], B.qcn[t]));
+      st_site(dst + e, cscale(B.Mat[pr * c + j], B.qcn[t]), B.key(l, 1), e);
     }
     // U S with U = J^dag (the product of the rotations is accumulated in B.U;
     // the previous US was consumed when Mat was formed)
@@ -1073,7 +1129,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     }
     __syncthreads();
     const T inv = B.amps[0].re;
-    for (int e = threadIdx.x; e < c; e += blockDim.x) st(A + e, cscale(B.Mat[e], inv));
+    for (int e = threadIdx.x; e < c; e += blockDim.x) st_site(A + e, cscale(B.Mat[e], inv), B.key(0, 1), e);
     __syncthreads();
   }
   if (env_nt > 0) {  // sites folded..1 are final, site 0 just renormalised
@@ -1160,6 +1216,91 @@ __device__ void chain_targets(Blk<T, S>& B, int nt) {
   __syncthreads();
 }
 
+// ------------------------------------------------------------ block set-up
+// Point a block's working state at its shared-memory plan, copy the chain in
+// when it is resident, and load the instance's bond table and counters
+// (log-norm reset to zero when zero_log_norm).  Ends with a block barrier.
+template <class T, class S>
+__device__ void blk_open(Blk<T, S>& B, const InstDesc& d, unsigned char* smem, bool zero_log_norm) {
+  const int n = d.n;
+  const size_t site_bytes = d.resident ? (size_t)d.site_off[n] * sizeof(S) : 0;
+  const SmemPlan P = make_plan(n, d.M, d.xcap, d.chicap, sizeof(T), site_bytes);
+  B.d = &d;
+  B.n = n;
+  {
+    int* so = (int*)(smem + P.off_soff);
+    for (int l = threadIdx.x; l <= n; l += blockDim.x) so[l] = (int)d.site_off[l];
+    B.off = so;
+  }
+  B.chi = (int*)(smem + P.off_chi);
+  B.qb = (int*)(smem + P.off_qb);
+  unsigned char* tb = smem + P.off_terms;
+  B.tbits = (unsigned long long*)tb;
+  B.tcoef = (cx<T>*)(tb + sizeof(unsigned long long) * (d.M + 2));
+  B.tplus = (int*)(tb + (sizeof(unsigned long long) + 2 * sizeof(T)) * (d.M + 2));
+  B.amps = (cx<T>*)(smem + P.off_amps);
+  B.misc = (int*)(smem + P.off_misc);
+  B.dmisc = (double*)(smem + P.off_misc + 128);
+  B.tmisc = (T*)(smem + P.off_misc + 256);
+  B.Rp = (cx<T>*)(smem + P.off_rprev);
+  B.W = (cx<T>*)(smem + P.off_w);
+  B.tau = (T*)(smem + P.off_tau);
+  B.beta = (cx<T>*)(smem + P.off_beta);
+  B.Mat = (cx<T>*)(smem + P.off_mat);
+  B.U = (cx<T>*)(smem + P.off_u);
+  B.US = (cx<T>*)(smem + P.off_us);
+  B.sig = (T*)(smem + P.off_sig);
+  B.perm = (int*)(smem + P.off_perm);
+  B.qperm = (int*)(smem + P.off_qperm);
+  B.qcn = (T*)(smem + P.off_qcn);
+  B.tbuf = smem + P.off_tbuf;
+  S* gsites = (S*)d.sites;
+  if (d.resident) {
+    S* ssites = (S*)(smem + P.off_sites);
+    for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) ssites[e] = gsites[e];
+    B.sites = ssites;
+  } else {
+    B.sites = gsites;
+  }
+  DevStats* ds = d.stats;
+  for (int l = threadIdx.x; l <= n; l += blockDim.x) B.chi[l] = ds->chi[l];
+  if (threadIdx.x == 0) {
+    B.misc[0] = ds->status;
+    B.misc[1] = ds->max_jacobi_sweeps;
+    B.misc[2] = 0;
+    B.misc[3] = 0;
+    B.dmisc[0] = zero_log_norm ? 0.0 : ds->log_norm;
+    B.dmisc[1] = ds->discarded;
+    B.tmisc[0] = (T)d.trunc_eps;
+    B.misc[5] = d.trunc_dim;
+    B.tmisc[1] = (T)d.tol;
+    B.tmisc[2] = (T)0;
+  }
+  __syncthreads();
+}
+
+// Write a block's chain (when resident), bond table and counters back.
+template <class T, class S>
+__device__ void blk_close(Blk<T, S>& B, const InstDesc& d) {
+  __syncthreads();
+  const int n = d.n;
+  if (d.resident) {
+    S* gsites = (S*)d.sites;
+    const S* ssites = B.sites;
+    for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) gsites[e] = ssites[e];
+  }
+  DevStats* ds = d.stats;
+  for (int l = threadIdx.x; l <= n; l += blockDim.x) ds->chi[l] = B.chi[l];
+  if (threadIdx.x == 0) {
+    ds->status = B.misc[0];
+    ds->max_jacobi_sweeps = B.misc[1];
+    ds->jacobi_sweeps += B.misc[2];
+    ds->svd_count += B.misc[3];
+    ds->log_norm = B.dmisc[0];
+    ds->discarded = B.dmisc[1] + (double)B.tmisc[2];
+  }
+}
+
 // ------------------------------------------------------------ the kernel
 template <class T, class S, class CR>
 __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int count, int* queue) {
@@ -1175,62 +1316,10 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
     const unsigned long long t_begin = global_ns();
     const InstDesc& d = descs[idx];
     const int n = d.n;
-    size_t site_bytes = 0;
-    if (d.resident) site_bytes = (size_t)d.site_off[n] * sizeof(S);
-    const SmemPlan P = make_plan(n, d.M, d.xcap, d.chicap, sizeof(T), site_bytes);
     Blk<T, S> B;
-    B.d = &d;
-    B.n = n;
-    {
-      int* so = (int*)(smem + P.off_soff);
-      for (int l = threadIdx.x; l <= n; l += blockDim.x) so[l] = (int)d.site_off[l];
-      B.off = so;
-    }
-    B.chi = (int*)(smem + P.off_chi);
-    B.qb = (int*)(smem + P.off_qb);
-    unsigned char* tb = smem + P.off_terms;
-    B.tbits = (unsigned long long*)tb;
-    B.tcoef = (cx<T>*)(tb + sizeof(unsigned long long) * (d.M + 2));
-    B.tplus = (int*)(tb + (sizeof(unsigned long long) + 2 * sizeof(T)) * (d.M + 2));
-    B.amps = (cx<T>*)(smem + P.off_amps);
-    B.misc = (int*)(smem + P.off_misc);
-    B.dmisc = (double*)(smem + P.off_misc + 128);
-    B.tmisc = (T*)(smem + P.off_misc + 256);
-    B.Rp = (cx<T>*)(smem + P.off_rprev);
-    B.W = (cx<T>*)(smem + P.off_w);
-    B.tau = (T*)(smem + P.off_tau);
-    B.beta = (cx<T>*)(smem + P.off_beta);
-    B.Mat = (cx<T>*)(smem + P.off_mat);
-    B.U = (cx<T>*)(smem + P.off_u);
-    B.US = (cx<T>*)(smem + P.off_us);
-    B.sig = (T*)(smem + P.off_sig);
-    B.perm = (int*)(smem + P.off_perm);
-    B.qperm = (int*)(smem + P.off_qperm);
-    B.qcn = (T*)(smem + P.off_qcn);
-    B.tbuf = smem + P.off_tbuf;
-    S* gsites = (S*)d.sites;
-    if (d.resident) {
-      S* ssites = (S*)(smem + P.off_sites);
-      for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) ssites[e] = gsites[e];
-      B.sites = ssites;
-    } else {
-      B.sites = gsites;
-    }
+    B.rng = 0;
+    blk_open(B, d, smem, false);
     DevStats* ds = d.stats;
-    for (int l = threadIdx.x; l <= n; l += blockDim.x) B.chi[l] = ds->chi[l];
-    if (threadIdx.x == 0) {
-      B.misc[0] = ds->status;
-      B.misc[1] = ds->max_jacobi_sweeps;
-      B.misc[2] = 0;
-      B.misc[3] = 0;
-      B.dmisc[0] = ds->log_norm;
-      B.dmisc[1] = ds->discarded;
-      B.tmisc[0] = (T)d.trunc_eps;
-      B.misc[5] = d.trunc_dim;
-      B.tmisc[1] = (T)d.tol;
-      B.tmisc[2] = (T)0;
-    }
-    __syncthreads();
     const int M = d.M;
     long long done = 0;
     // fused form: <w|psi> and <s|psi> for the next iteration come out of the
@@ -1239,8 +1328,13 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
     const int envG = pow2_cap32(d.chicap);
     const int env_nt = (d.apply == 2 && n >= 2 && blockDim.x >= 64 && envG <= 16 && M + 1 <= 32 / envG) ? M + 1 : 0;
     bool amps_ready = false;
+    const long long it0 = ds->iterations;  // iterations applied before this launch
+    // rounding keys: per instance (its marked strings) and per iteration
+    unsigned long long salt = fmix64(((unsigned long long)n << 8) | (unsigned long long)M);
+    for (int t = 0; t < M; ++t) salt = fmix64(salt ^ d.marked[t]);
     for (long long it = 0; it < d.k; ++it) {
       if (B.misc[0] != 0) break;
+      B.rng = salt + ((unsigned long long)(it0 + it) << 3);
       const long long pi = d.phase_offset + it;
       if (d.rec) {
         // record <w|psi> for every marked w and <s|psi> (adjoint recompute)
@@ -1333,20 +1427,9 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
       __syncthreads();
       if (B.misc[0] == 0) ++done;
     }
-    __syncthreads();
-    if (d.resident) {
-      const S* ssites = B.sites;
-      for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) gsites[e] = ssites[e];
-    }
-    for (int l = threadIdx.x; l <= n; l += blockDim.x) ds->chi[l] = B.chi[l];
+    blk_close(B, d);
     if (threadIdx.x == 0) {
       ds->iterations += done;
-      ds->status = B.misc[0];
-      ds->max_jacobi_sweeps = B.misc[1];
-      ds->jacobi_sweeps += B.misc[2];
-      ds->svd_count += B.misc[3];
-      ds->log_norm = B.dmisc[0];
-      ds->discarded = B.dmisc[1] + (double)B.tmisc[2];
       ds->t_begin = t_begin;
       ds->t_end = global_ns();
       ds->sm = sm_id();
@@ -1458,61 +1541,9 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
   double* gphi = aa.gphi;
   double* gpsi = aa.gpsi;
   const int n = d.n, M = d.M;
-  size_t site_bytes = d.resident ? (size_t)d.site_off[n] * sizeof(S) : 0;
-  const SmemPlan P = make_plan(n, M, d.xcap, d.chicap, sizeof(T), site_bytes);
   Blk<T, S> B;
-  B.d = &d;
-  B.n = n;
-  {
-    int* so = (int*)(smem + P.off_soff);
-    for (int l = threadIdx.x; l <= n; l += blockDim.x) so[l] = (int)d.site_off[l];
-    B.off = so;
-  }
-  B.chi = (int*)(smem + P.off_chi);
-  B.qb = (int*)(smem + P.off_qb);
-  unsigned char* tb = smem + P.off_terms;
-  B.tbits = (unsigned long long*)tb;
-  B.tcoef = (cx<T>*)(tb + sizeof(unsigned long long) * (M + 2));
-  B.tplus = (int*)(tb + (sizeof(unsigned long long) + 2 * sizeof(T)) * (M + 2));
-  B.amps = (cx<T>*)(smem + P.off_amps);
-  B.misc = (int*)(smem + P.off_misc);
-  B.dmisc = (double*)(smem + P.off_misc + 128);
-  B.tmisc = (T*)(smem + P.off_misc + 256);
-  B.qperm = (int*)(smem + P.off_qperm);
-  B.qcn = (T*)(smem + P.off_qcn);
-  B.tbuf = smem + P.off_tbuf;
-  B.Rp = (cx<T>*)(smem + P.off_rprev);
-  B.W = (cx<T>*)(smem + P.off_w);
-  B.tau = (T*)(smem + P.off_tau);
-  B.beta = (cx<T>*)(smem + P.off_beta);
-  B.Mat = (cx<T>*)(smem + P.off_mat);
-  B.U = (cx<T>*)(smem + P.off_u);
-  B.US = (cx<T>*)(smem + P.off_us);
-  B.sig = (T*)(smem + P.off_sig);
-  B.perm = (int*)(smem + P.off_perm);
-  S* gsites = (S*)d.sites;
-  if (d.resident) {
-    S* ssites = (S*)(smem + P.off_sites);
-    for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) ssites[e] = gsites[e];
-    B.sites = ssites;
-  } else {
-    B.sites = gsites;
-  }
-  DevStats* ds = d.stats;
-  for (int l = threadIdx.x; l <= n; l += blockDim.x) B.chi[l] = ds->chi[l];
-  if (threadIdx.x == 0) {
-    B.misc[0] = ds->status;
-    B.misc[1] = ds->max_jacobi_sweeps;
-    B.misc[2] = 0;
-    B.misc[3] = 0;
-    B.dmisc[0] = project ? 0.0 : ds->log_norm;
-    B.dmisc[1] = ds->discarded;
-    B.tmisc[0] = (T)d.trunc_eps;
-    B.misc[5] = d.trunc_dim;
-    B.tmisc[1] = (T)d.tol;
-    B.tmisc[2] = (T)0;
-  }
-  __syncthreads();
+  B.rng = 0x2000000000000000ull;
+  blk_open(B, d, smem, project != 0);
   // targets: the marked strings (t < M) and |s> = |+>^n (t = M)
   for (int t = threadIdx.x; t <= M; t += blockDim.x) {
     B.tbits[t] = t < M ? d.marked[t] : 0ull;
@@ -1537,6 +1568,7 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
     amps_ready = env_nt > 0;
   }
   for (long long k = k_hi; k > k_lo && B.misc[0] == 0; --k) {
+    B.rng = ((unsigned long long)k << 3) | 0x4000000000000000ull;
     if (!fused) {
       adjoint_two_steps<T, S, CR>(B, rec, k, k_lo, phi, psi, scale, gphi, gpsi);
       continue;
@@ -1587,20 +1619,61 @@ __global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, con
     sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), M + 1, env_nt);
     amps_ready = env_nt > 0;
   }
+  blk_close(B, d);
+}
+
+// ------------------------------------------------------------ gate-level circuit
+// One-qubit gate u on site l, in place: A[i, s, j] <- sum_s' u[s][s'] A[i, s', j].
+// A unitary on the physical index keeps a right-orthonormal site
+// right-orthonormal, so the chain stays canonical.
+template <class T, class S>
+__device__ void apply_1q(Blk<T, S>& B, int l, const double* u) {
+  const int cl = B.chi[l], cr = B.chi[l + 1];
+  S* A = B.slot(l);
+  const cx<T> u00 = mk<T>((T)u[0], (T)u[1]), u01 = mk<T>((T)u[2], (T)u[3]);
+  const cx<T> u10 = mk<T>((T)u[4], (T)u[5]), u11 = mk<T>((T)u[6], (T)u[7]);
+  for (int e = threadIdx.x; e < cl * cr; e += blockDim.x) {
+    const int i = e / cr, j = e % cr;
+    const cx<T> a0 = ld<T>(A + (i * 2) * cr + j), a1 = ld<T>(A + (i * 2 + 1) * cr + j);
+    st_site(A + (i * 2) * cr + j, cmac(cmul(u00, a0), u01, a1), B.key(l, 2), (unsigned)((i * 2) * cr + j));
+    st_site(A + (i * 2 + 1) * cr + j, cmac(cmul(u10, a0), u11, a1), B.key(l, 2), (unsigned)((i * 2 + 1) * cr + j));
+  }
   __syncthreads();
-  if (d.resident) {
-    const S* ssites = B.sites;
-    for (long long e = threadIdx.x; e < d.site_off[n]; e += blockDim.x) gsites[e] = ssites[e];
+}
+
+// Gate-level simulation of one instance (one thread block): `repeat` passes
+// over `count` gates.  A one-qubit gate updates its site tensor in place; a
+// multi-controlled phase I - (1 - e^{i phase}) |1...1><1...1| is the MPO of
+// bond 2 diag(I, |1><1|) with left boundary (1, e^{i phase} - 1) -- the
+// oracle MPO of the all-ones string, d.marked[0] -- contracted into the sites
+// and recompressed by the QR and truncated SVD sweeps.
+template <class T, class S, class CR>
+__global__ void __launch_bounds__(256) circuit_kernel(const InstDesc* descs, const GateOp* gates, long long count,
+                                                       long long repeat) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const InstDesc& d = descs[0];
+  Blk<T, S> B;
+  B.rng = 0x1000000000000000ull;
+  blk_open(B, d, smem, false);
+  for (long long r = 0; r < repeat && B.misc[0] == 0; ++r) {
+    for (long long g = 0; g < count && B.misc[0] == 0; ++g) {
+      const GateOp& op = gates[g];
+      B.rng = fmix64(B.rng + 0x9e3779b97f4a7c15ull);
+      if (op.kind == 0) {
+        apply_1q(B, op.site, op.u);
+      } else {
+        if (threadIdx.x == 0) {
+          double sp, cp;
+          sincos(op.u[0], &sp, &cp);
+          B.tcoef[0] = mk<T>(1, 0);
+          B.tcoef[1] = mk<T>((T)(cp - 1.0), (T)sp);
+        }
+        __syncthreads();
+        sweep_pair<T, S, CR>(B, 0, 0, 2, B.tcoef, mk<T>(1, 0), 0);
+      }
+    }
   }
-  for (int l = threadIdx.x; l <= n; l += blockDim.x) ds->chi[l] = B.chi[l];
-  if (threadIdx.x == 0) {
-    ds->status = B.misc[0];
-    ds->max_jacobi_sweeps = B.misc[1];
-    ds->jacobi_sweeps += B.misc[2];
-    ds->svd_count += B.misc[3];
-    ds->log_norm = B.dmisc[0];
-    ds->discarded = B.dmisc[1] + (double)B.tmisc[2];
-  }
+  blk_close(B, d);
 }
 
 // ------------------------------------------------------------------ init
@@ -1858,6 +1931,17 @@ cudaError_t FormLaunch<T, S, CR>::sample(const InstDesc* d_desc, int inst, int c
     sample_kernel<S, 64><<<(unsigned)grid, threads, 0, stream>>>(d_desc, inst, shots, seed, d_bits, d_margin);
   else
     return cudaErrorInvalidValue;
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <class T, class S, class CR>
+cudaError_t FormLaunch<T, S, CR>::circuit(const InstDesc* d_desc, const GateOp* d_gates, long long count,
+                                          long long repeat, int threads, size_t smem, cudaStream_t stream) {
+  auto k = circuit_kernel<T, S, CR>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<1, threads, smem, stream>>>(d_desc, d_gates, count, repeat);
   count_launch(1);
   return cudaGetLastError();
 }

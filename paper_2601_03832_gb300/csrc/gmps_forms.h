@@ -25,6 +25,8 @@ struct FormLaunch {
   static cudaError_t sample(const InstDesc* d_desc, int inst, int chmax, long long shots, unsigned long long seed,
                             unsigned long long* d_bits, double* d_margin, cudaStream_t stream);
   static cudaError_t copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int count, cudaStream_t stream);
+  static cudaError_t circuit(const InstDesc* d_desc, const GateOp* d_gates, long long count, long long repeat,
+                             int threads, size_t smem, cudaStream_t stream);
 };
 
 using FormC128 = FormLaunch<double, double2, double>;  // GMPS_C128

@@ -61,6 +61,13 @@ struct InstDesc {
                             // <s|psi> of the chain, (M+1) complex per iteration
 };
 
+// One gate of a gate-level circuit (same layout as the public gmps_gate).
+struct GateOp {
+  int kind;      // 0: 2x2 unitary u on qubit `site`; 1: multi-controlled phase on all n qubits
+  int site;
+  double u[8];   // kind 0: u00, u01, u10, u11 as (re, im); kind 1: u[0] = phase
+};
+
 // Per-chain arguments of the adjoint kernel (one entry per costate chain).
 struct AdjArgs {
   const double* rec;   // forward chain's marked amplitudes and <s|psi> of the segment
@@ -149,6 +156,8 @@ cudaError_t launch_adjoint(const InstDesc* d_mu, const AdjArgs* d_args, int coun
                            size_t smem, long long k_lo, long long k_hi, int project, cudaStream_t stream);
 cudaError_t launch_batch_prob(const InstDesc* d_desc, int count, int dtype, double* d_p,
                               cudaStream_t stream);
+cudaError_t launch_circuit(const InstDesc* d_desc, const GateOp* d_gates, long long count, long long repeat,
+                           int dtype, int threads, size_t smem, cudaStream_t stream);
 size_t storage_bytes(int dtype);      // bytes of one complex site element
 size_t linalg_real_bytes(int dtype);  // bytes of one linear-algebra real
 int max_smem_optin();

@@ -60,4 +60,9 @@ cudaError_t launch_copy_sites(const InstDesc* d_src, const InstDesc* d_dst, int 
   return GMPS_DISPATCH(dtype, copy_sites(d_src, d_dst, count, stream));
 }
 
+cudaError_t launch_circuit(const InstDesc* d_desc, const GateOp* d_gates, long long count, long long repeat,
+                           int dtype, int threads, size_t smem, cudaStream_t stream) {
+  return GMPS_DISPATCH(dtype, circuit(d_desc, d_gates, count, repeat, threads, smem, stream));
+}
+
 }  // namespace gmps

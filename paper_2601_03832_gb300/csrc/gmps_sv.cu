@@ -15,7 +15,20 @@
 // the new marked amplitudes (double-buffered by iteration parity) and the
 // iteration count for the next pass.  The iteration index lives in device
 // memory, so every launch is identical and k launches replay from a CUDA
-// graph.  Sums and coefficients are FP64 in both storage forms.
+// graph.  Coefficients, block sums and totals are FP64.
+//
+// On this part the FP64 pipe (measured 1.06 TFLOP/s for the chip) would bind
+// a pass that spends four FP64 additions per amplitude (the update and the
+// running sum): 32 bytes per 4 DADDs is ~4.2 TB/s.  So each thread keeps its
+// running sum on the FP32 pipes instead: every FP64 value is split exactly by
+// bit manipulation into a truncated FP32 head (24 significant bits) and the
+// round-to-nearest FP32 value of the remainder (error below 2^-48 |v|,
+// unbiased); heads accumulate with Knuth's TwoSum (error-free), remainders
+// with plain FP32 adds, and the thread's three FP32 partials are added in
+// FP64 once at the end.  The complex128 update c - v stays FP64 (two DADDs
+// per amplitude); the complex64 form updates in FP32 with c as a double-word
+// pair (c_hi + c_lo), one rounding per stored value, and never touches the
+// FP64 pipe in its loop.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,6 +74,11 @@ __device__ __forceinline__ double2 ld_amp(const float2* p) {
 }
 __device__ __forceinline__ void st_amp(double2* p, double2 v) { __stcs(p, v); }
 __device__ __forceinline__ void st_amp(float2* p, double2 v) { __stcs(p, make_float2((float)v.x, (float)v.y)); }
+// a stored value as FP64, and an FP64 value known to be a stored value back
+__device__ __forceinline__ double2 widen(double2 v) { return v; }
+__device__ __forceinline__ double2 widen(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 narrow(double2 v, const double2*) { return v; }
+__device__ __forceinline__ float2 narrow(double2 v, const float2*) { return make_float2((float)v.x, (float)v.y); }
 // the value as stored (rounded to the storage type)
 __device__ __forceinline__ double2 as_stored(double2 v, const double2*) { return v; }
 __device__ __forceinline__ double2 as_stored(double2 v, const float2*) {
@@ -74,6 +92,35 @@ __device__ __forceinline__ void phases_of(const SvState& s, long long it, double
   if (s.phase[0]) sincos(s.phase[0][j], &sphi, &cphi);
   if (s.phase[1]) sincos(s.phase[1][j], &spsi, &cpsi);
 }
+
+// FP32 running sum of FP64 values (see the file comment): TwoSum of the heads,
+// plain sum of the remainders.
+struct Acc32 {
+  float s = 0.f, e = 0.f, r = 0.f;
+  __device__ __forceinline__ void add_f32(float v) {
+    const float t = __fadd_rn(s, v);
+    const float z = __fsub_rn(t, s);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(v, z)));
+    s = t;
+  }
+  __device__ __forceinline__ void add(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32);
+    const unsigned E = (hi >> 20) & 0x7ffu;
+    if (E < 1023u - 100u) return;  // |x| < 2^-100: below every sum this pass forms
+    // head: the top 24 significant bits, exactly an FP32 value
+    const unsigned m = ((hi & 0xfffffu) << 3) | ((unsigned)b >> 29);
+    add_f32(__uint_as_float((hi & 0x80000000u) | ((E - 1023u + 127u) << 23) | m));
+    // remainder: the low 29 bits times 2^(E-1075), rounded to nearest FP32
+    const float low = __uint2float_rn((unsigned)b & 0x1fffffffu);
+    const int ex = (int)E - 1075;  // >= -198: scale in two exact steps
+    const float sc1 = __uint_as_float((unsigned)(ex / 2 + 127) << 23);
+    const float sc2 = __uint_as_float((unsigned)(ex - ex / 2 + 127) << 23);
+    const float rv = __fmul_rn(__fmul_rn(low, sc1), sc2);
+    r = __fadd_rn(r, (hi & 0x80000000u) ? -rv : rv);
+  }
+  __device__ __forceinline__ double value() const { return ((double)s + (double)e) + (double)r; }
+};
 
 // Block-wide FP64 complex sum in a fixed order (warp shuffles, then warp 0).
 __device__ __forceinline__ double2 block_sum(double2 a, double2* sh) {
@@ -94,6 +141,38 @@ __device__ __forceinline__ double2 block_sum(double2 a, double2* sh) {
   }
   __syncthreads();
   return r;  // valid in thread 0
+}
+
+// v -> c - v in the storage type: FP64 for complex128; for complex64 in FP32
+// with c = c_hi + c_lo (double-word), rounded once.
+template <class S>
+struct Upd;
+template <>
+struct Upd<double2> {
+  double2 c;
+  __device__ explicit Upd(double2 c_) : c(c_) {}
+  __device__ __forceinline__ double2 operator()(double2 x) const { return make_double2(c.x - x.x, c.y - x.y); }
+};
+template <>
+struct Upd<float2> {
+  float hr, lr, hi_, li;
+  __device__ explicit Upd(double2 c) {
+    hr = (float)c.x;
+    lr = (float)(c.x - (double)hr);
+    hi_ = (float)c.y;
+    li = (float)(c.y - (double)hi_);
+  }
+  __device__ __forceinline__ float2 operator()(float2 x) const {
+    return make_float2(__fadd_rn(__fsub_rn(hr, x.x), lr), __fadd_rn(__fsub_rn(hi_, x.y), li));
+  }
+};
+__device__ __forceinline__ void acc_add(Acc32& ar, Acc32& ai, double2 y) {
+  ar.add(y.x);
+  ai.add(y.y);
+}
+__device__ __forceinline__ void acc_add(Acc32& ar, Acc32& ai, float2 y) {
+  ar.add_f32(y.x);
+  ai.add_f32(y.y);
 }
 
 template <class S>
@@ -122,31 +201,28 @@ __global__ void __launch_bounds__(kSvThreads) sv_pass(S* v, SvState s) {
   }
   __syncthreads();
   const double2 c = c_sh;
-  // stream v(x) <- c - v(x), summing the stored values
-  double2 acc = make_double2(0.0, 0.0);
+  // stream v(x) <- c - v(x), summing the stored values on the FP32 pipes
+  Acc32 ar, ai;
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const Upd<S> up(c);
   for (; i + (kSvUnroll - 1) * stride < s.N; i += kSvUnroll * stride) {
-    double2 x[kSvUnroll];
+    S x[kSvUnroll];
 #pragma unroll
-    for (int u = 0; u < kSvUnroll; ++u) x[u] = ld_amp(v + i + u * stride);
+    for (int u = 0; u < kSvUnroll; ++u) x[u] = __ldcs(v + i + u * stride);
 #pragma unroll
     for (int u = 0; u < kSvUnroll; ++u) {
-      const double2 y = make_double2(c.x - x[u].x, c.y - x[u].y);
-      st_amp(v + i + u * stride, y);
-      const double2 ys = as_stored(y, v);
-      acc.x += ys.x;
-      acc.y += ys.y;
+      const S y = up(x[u]);
+      __stcs(v + i + u * stride, y);
+      acc_add(ar, ai, y);
     }
   }
   for (; i < s.N; i += stride) {
-    const double2 x = ld_amp(v + i);
-    const double2 y = make_double2(c.x - x.x, c.y - x.y);
-    st_amp(v + i, y);
-    const double2 ys = as_stored(y, v);
-    acc.x += ys.x;
-    acc.y += ys.y;
+    const S y = up(__ldcs(v + i));
+    __stcs(v + i, y);
+    acc_add(ar, ai, y);
   }
+  const double2 acc = make_double2(ar.value(), ai.value());
   const double2 bs = block_sum(acc, sh);
   if (threadIdx.x == 0) {
     s.part[blockIdx.x] = bs;
@@ -175,7 +251,7 @@ __global__ void __launch_bounds__(kSvThreads) sv_pass(S* v, SvState s) {
       // v'(w) = c - e^{i phi} v(w); the pass wrote c - v(w)
       const double2 y = make_double2(c.x - (cphi * w.x - sphi * w.y), c.y - (cphi * w.y + sphi * w.x));
       S* dst = v + s.marked[t];
-      const double2 old = as_stored(make_double2(c.x - w.x, c.y - w.y), v);
+      const double2 old = widen(up(narrow(w, v)));  // exactly what the pass stored there
       st_amp(dst, y);
       const double2 ys = as_stored(y, v);
       mk_next[t] = ys;

@@ -200,7 +200,7 @@ __device__ int tiny_qr_factor(cx<T> w0, int m, int n, T floor_rel2, cx<T>* Rp, c
 // H_0 ... H_{p-1} e_c is built in the lanes of column c; the
   // first factor applied is H_{p-1} e_c = e_c - v conj(v_c) (no reduction).
 template <class T, class S>
-__device__ void tiny_q_store(cx<T> a, int m, int p, S* dst) {
+__device__ void tiny_q_store(cx<T> a, int m, int p, S* dst, unsigned long long key) {
   const int lane = threadIdx.x & 31;
   const int c = lane >> 3, i = lane & 7;
   const cx<T> zero = mk<T>(0, 0);
@@ -222,7 +222,7 @@ __device__ void tiny_q_store(cx<T> a, int m, int p, S* dst) {
     const cx<T> d = mk<T>(shidx(t, g0), shidx(t, g0 + 4));
     if (in) q = cmac(q, vj, mk<T>(-d.re, -d.im));
   }
-  if (c < p && i < m) st(dst + i * p + c, q);
+  if (c < p && i < m) st_site(dst + i * p + c, q, key, i * p + c);
 }
 
 // Hand-off of a small QR step between warps: two buffers (by site parity),
@@ -387,7 +387,7 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
   if (row && myrank < k) {
     const T inv = rsqrt(sp);
     if (inM) {
-      st(A + myrank * c + j, cscale(x, inv));
+      st_site(A + myrank * c + j, cscale(x, inv), B.key(l, 1), myrank * c + j);
     } else if (inU) {
       const T sg = sp * inv;  // sigma = sigma^2 / sigma
       B.US[(j - c) * k + myrank] = mk<T>(x.re * sg, -(x.im * sg));

@@ -12,7 +12,16 @@ Everything below runs on the CUDA library through the binding; nothing here
 computes a reference value.  The marked string for n qubits is drawn from
 seed 1000 + n (SplitMix64, `inputs.marked_strings`).
 
+It also compares the iterative MPS path with the iterative statevector path
+(grover_sv_*, Sec. III-B-1) over n -- the crossover of Sec. IV-1 --, the
+gate-level "Common" and "Iterative" methods of Sec. III-A (Fig. 1), and runs
+single instances for profiling.
+
 Run: python -m paper_2601_03832_gb300.experiments [--ns 10-29] [--shots-ns 2-29]
+     python -m paper_2601_03832_gb300.experiments crossover [--ns 12-31] [--sv-max-iters 400]
+     python -m paper_2601_03832_gb300.experiments circuits [--ns 10-29] [--kmax K]
+     python -m paper_2601_03832_gb300.experiments single --n 29 --k 50 [--M 1] [--dtype c128] [--apply fused]
+         [--path mps|sv]
 """
 from __future__ import annotations
 
@@ -82,12 +91,147 @@ def shot_sweep(ns, shots=SHOT_COUNTS, sample_seed=2, dtype="c128", chi_max=4, ap
     return rows
 
 
+def crossover_sweep(ns, sv_max_iters=400, mps_max_iters=4000, chi_max=4):
+    """Iterations/s of the iterative MPS path (FP64, fused) and of the
+    iterative statevector path (complex128) for M = 1 at each n, each timed
+    with CUDA events on a slice of min(k, max_iters) iterations of the
+    k_paper(n) run (a statevector pass costs the same at every iteration),
+    and the predicted full-run seconds.  The statevector path is skipped
+    where its 2^n x 16 bytes do not fit the device."""
+    import torch
+    stream = torch.cuda.current_stream()
+    free, _ = torch.cuda.mem_get_info()
+    rows = []
+    for n in ns:
+        w, k = marked_for(n), k_paper(n)
+        row = {"n": n, "k": k}
+        km = min(k, mps_max_iters)
+        g = binding.GroverMPS(n, [w], dtype="c128", apply="fused", chi_max=chi_max, stream=stream.cuda_stream)
+        g.iterate(2)
+        g.reset()
+        a, b = _events()
+        a.record(stream)
+        g.iterate(km)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1000.0
+        row["mps"] = {"iterations_per_s": km / sec, "timed_iterations": km, "full_run_s": k * sec / km}
+        g.close()
+        if (16 << n) < 0.8 * free:
+            ks = min(k, sv_max_iters)
+            v = binding.GroverSV(n, [w], dtype="c128", stream=stream.cuda_stream)
+            v.iterate(min(ks, 70))        # warm-up: graph instantiation
+            v.reset()
+            a, b = _events()
+            a.record(stream)
+            v.iterate(ks)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / 1000.0
+            row["sv"] = {"iterations_per_s": ks / sec, "timed_iterations": ks, "full_run_s": k * sec / ks,
+                         "hbm_gbs": 32.0 * (1 << n) * ks / sec / 1e9}
+            v.close()
+        rows.append(row)
+    cross = None
+    for r in rows:
+        if "sv" in r and r["mps"]["iterations_per_s"] > r["sv"]["iterations_per_s"]:
+            cross = r["n"]
+            break
+    return rows, cross
+
+
+def common_vs_iterative(ns, chi_max=4, kmax=None):
+    """The paper's two gate-level methods (Sec. III-A, Fig. 1) on this GPU for
+    M = 1 and k = k_paper(n) (capped at kmax): "Common" builds the whole
+    k-iteration circuit (H, X and multi-controlled Z gates) and applies it
+    once; "Iterative" builds one iteration's gates and applies them k times
+    to the state it keeps.  Both run gate by gate through
+    grover_mps_apply_circuit; wall seconds include building the gate list on
+    the host and copying it to the device.  The fused direct-sum iteration
+    (one sweep pair per Grover gate) is timed beside them."""
+    import time
+
+    import torch
+    rows = []
+    for n in ns:
+        w, k = marked_for(n), k_paper(n)
+        if kmax:
+            k = min(k, kmax)
+        row = {"n": n, "k": k}
+        for method in ("iterative", "common"):
+            g = binding.GroverMPS(n, [w], dtype="c128", apply="mpo", chi_max=chi_max)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gates = binding.grover_gates(n, [w], 1 if method == "iterative" else k)
+            g.apply_circuit(gates, repeat=k if method == "iterative" else 1)
+            p = g.prob_marked()
+            sec = time.perf_counter() - t0
+            row[method] = {"seconds": sec, "P_marked": p, "gates": len(gates),
+                           "gate_list_bytes": len(gates) * 72}
+            g.close()
+        g = binding.GroverMPS(n, [w], dtype="c128", apply="fused", chi_max=chi_max)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.iterate(k)
+        row["fused"] = {"seconds": time.perf_counter() - t0, "P_marked": g.prob_marked()}
+        g.close()
+        row["common_over_iterative"] = row["common"]["seconds"] / row["iterative"]["seconds"]
+        rows.append(row)
+    return rows
+
+
+def single(n, M, k, dtype="c128", apply="fused", chi_max=None, path="mps", seed=None):
+    """One instance (marked strings from seed 1000 + n unless `seed`): k
+    iterations on the MPS or statevector path, P_marked printed.  A small,
+    fixed case for profiling the kernels."""
+    marked = inputs.marked_strings(n, M, seed=1000 + n if seed is None else seed)
+    if path == "sv":
+        g = binding.GroverSV(n, marked, dtype=dtype)
+    else:
+        g = binding.GroverMPS(n, marked, dtype=dtype, apply=apply, chi_max=chi_max or M + 3)
+    g.iterate(k)
+    p = g.prob_marked()
+    g.close()
+    return {"n": n, "M": M, "k": k, "dtype": dtype, "path": path, "P_marked": p}
+
+
 def _range(text: str):
     lo, _, hi = text.partition("-")
     return list(range(int(lo), int(hi or lo) + 1))
 
 
 def main(argv=None):
+    argv = list(sys.argv[1:] if argv is None else argv)
+    if argv and argv[0] == "crossover":
+        ap = argparse.ArgumentParser(description="iterative MPS against iterative statevector over n")
+        ap.add_argument("--ns", default="12-31")
+        ap.add_argument("--sv-max-iters", type=int, default=400)
+        args = ap.parse_args(argv[1:])
+        binding.load()
+        rows, cross = crossover_sweep(_range(args.ns), sv_max_iters=args.sv_max_iters)
+        print(json.dumps({"rows": rows, "mps_faster_from_n": cross}))
+        return 0
+    if argv and argv[0] == "circuits":
+        ap = argparse.ArgumentParser(description="gate-level Common against Iterative")
+        ap.add_argument("--ns", default="10-29")
+        ap.add_argument("--kmax", type=int, default=None)
+        args = ap.parse_args(argv[1:])
+        binding.load()
+        print(json.dumps({"rows": common_vs_iterative(_range(args.ns), kmax=args.kmax)}))
+        return 0
+    if argv and argv[0] == "single":
+        ap = argparse.ArgumentParser(description="one instance")
+        ap.add_argument("--n", type=int, required=True)
+        ap.add_argument("--M", type=int, default=1)
+        ap.add_argument("--k", type=int, required=True)
+        ap.add_argument("--dtype", default="c128")
+        ap.add_argument("--apply", default="fused")
+        ap.add_argument("--chi-max", type=int, default=None)
+        ap.add_argument("--path", default="mps", choices=["mps", "sv"])
+        args = ap.parse_args(argv[1:])
+        binding.load()
+        print(json.dumps(single(args.n, args.M, args.k, args.dtype, args.apply, args.chi_max, args.path)))
+        return 0
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--ns", default="10-29", help="qubit counts of the precision and runtime sweep")
     ap.add_argument("--shots-ns", default="2-29", help="qubit counts of the shot sweep")

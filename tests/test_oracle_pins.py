@@ -312,3 +312,32 @@ def test_paper_iteration_count_rule():
     from paper_2601_03832_gb300.experiments import k_paper
     assert k_paper(12) == 50 and k_paper(29) == 18198 and k_paper(7) == 9
     assert [k_paper(n) for n in (2, 3, 4, 5)] == [2, 2, 3, 4]
+
+
+def test_gate_primitives_against_definitions():
+    """The dense one-qubit gate and multi-controlled phase: H on every qubit
+    of |0...0> is |s> (Eq. 2); X on qubit l flips bit l of a basis state;
+    the multi-controlled Z reflects only |1...1>; a one-qubit gate on qubit l
+    equals the Kronecker product I (x) u (x) I with u in bit position l."""
+    import numpy as np
+    from oracle import statevector as sv
+    n = 5
+    H = np.array([[1, 1], [1, -1]]) / np.sqrt(2)
+    X = np.array([[0, 1], [1, 0]])
+    v = np.zeros(1 << n, dtype=np.complex128)
+    v[0] = 1
+    for l in range(n):
+        v = sv.apply_1q(v, n, l, H)
+    assert np.allclose(v, sv.uniform_state(n), atol=1e-15)
+    e = np.zeros(1 << n, dtype=np.complex128)
+    e[0b00101] = 1
+    f = sv.apply_1q(e, n, 3, X)
+    assert f[0b01101] == 1 and np.count_nonzero(f) == 1
+    z = sv.apply_mcphase(np.ones(1 << n, dtype=np.complex128), np.pi)
+    assert abs(z[-1] + 1) < 1e-15 and np.all(z[:-1] == 1)
+    rng = np.random.default_rng(1)
+    u = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))
+    x = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    for l in range(n):
+        K = np.kron(np.kron(np.eye(1 << (n - 1 - l)), u), np.eye(1 << l))
+        assert np.allclose(sv.apply_1q(x, n, l, u), K @ x, atol=1e-13)
