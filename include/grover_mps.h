@@ -88,7 +88,11 @@ typedef enum {
   GMPS_APPLY_SPLIT = 1,
   /* G = D O as one direct sum of bond chi+M+1: one sweep pair per
    * iteration. */
-  GMPS_APPLY_FUSED = 2
+  GMPS_APPLY_FUSED = 2,
+  /* Gate-level circuits only (grover_mps_apply_circuit): bonds up to
+   * min(chi_max, 2^floor(n/2)) for general states, expanded bond 2 chi for
+   * the multi-controlled phases; grover_mps_iterate is refused. */
+  GMPS_APPLY_GATES = 3
 } gmps_apply;
 
 typedef struct gmps_config {
@@ -270,8 +274,9 @@ typedef struct gmps_gate {
  * contracted as an MPO of bond 2 and recompressed by the QR and truncated
  * SVD sweeps.  The paper's "Iterative" method passes the gates of one Grover
  * iteration with repeat = k, its "Common" method the k-iteration circuit with
- * repeat = 1.  Needs a handle whose expanded bond holds a bond-2 MPO (apply =
- * GMPS_APPLY_MPO, e.g. grover_mps_create).  Synchronises. */
+ * repeat = 1.  Needs a handle whose expanded bond holds a bond-2 MPO: apply =
+ * GMPS_APPLY_GATES (bonds up to chi_max, any circuit) or GMPS_APPLY_MPO
+ * (bonds sized for Grover states of the handle's M).  Synchronises. */
 gmps_status grover_mps_apply_circuit(gmps_handle h, const gmps_gate* gates, int64_t count, int64_t repeat);
 
 /* The gates of `iterations` Grover iterations as in Fig. 1A: for each marked

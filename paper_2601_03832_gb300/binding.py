@@ -16,9 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgrover_mps.so")
 
 GMPS_C128, GMPS_C64_F64SVD, GMPS_DW = 0, 1, 2
-GMPS_APPLY_MPO, GMPS_APPLY_SPLIT, GMPS_APPLY_FUSED = 0, 1, 2
+GMPS_APPLY_MPO, GMPS_APPLY_SPLIT, GMPS_APPLY_FUSED, GMPS_APPLY_GATES = 0, 1, 2, 3
 DTYPES = {"c128": GMPS_C128, "c64": GMPS_C64_F64SVD, "dw": GMPS_DW}
-APPLY = {"mpo": GMPS_APPLY_MPO, "split": GMPS_APPLY_SPLIT, "fused": GMPS_APPLY_FUSED}
+APPLY = {"mpo": GMPS_APPLY_MPO, "split": GMPS_APPLY_SPLIT, "fused": GMPS_APPLY_FUSED, "gates": GMPS_APPLY_GATES}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_TIMEOUT", 5: "ERR_NOCONV",
           6: "ERR_NUMERIC", 7: "ERR_STATE", 8: "ERR_CAPACITY", 9: "ERR_UNSUPPORTED"}
 

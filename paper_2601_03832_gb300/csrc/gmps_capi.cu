@@ -70,15 +70,27 @@ static RankRule rank_rule_for(int dtype) {
 // Launch and storage plan of one instance (host only; fixed size, so that
 // planning allocates nothing).
 struct Plan {
-  int chicap, xcap, threads, resident;
+  int chicap, xcap, rcap, threads, resident;
   size_t smem, site_elems, elem_bytes;
+  size_t work_bytes;         // device work area for the QR matrices (0: in shared memory)
   long long off[kMaxN + 1];  // slot offsets, n+1 used
 };
 
 static int xcap_for(int apply, int M, int chicap) {
   if (apply == GMPS_APPLY_MPO) return (M + 1) * chicap;
+  if (apply == GMPS_APPLY_GATES) return 2 * chicap;
   if (apply == GMPS_APPLY_SPLIT) return chicap + M;
   return chicap + M + 1;
+}
+
+// Rank capacity of a QR-sweep bond: the Schmidt rank of the state a QR step
+// factors.  O|psi> = |psi> + sum_w c_w |w> has rank <= chi + M and the
+// diffusion MPO of bond 2 at most doubles it, plus two for rounding-noise
+// directions at the rank-revealing QR's floor; the direct sums are bounded by
+// their expanded bond.  A rank above it raises GMPS_ERR_CAPACITY.
+static int rcap_for(int apply, int M, int chicap, int xcap) {
+  if (apply == GMPS_APPLY_MPO) return std::min(xcap, std::max(chicap + M, 2 * chicap) + 2);
+  return xcap;
 }
 
 // CTA size from the expanded bond; at least two warps, so that the small
@@ -109,7 +121,7 @@ static gmps_status validate(const gmps_config* c) {
   if (!(c->tol >= 0.0) || !std::isfinite(c->tol)) return fail(GMPS_ERR_ARG, "tol must be finite and >= 0");
   if (c->dtype != GMPS_C128 && c->dtype != GMPS_C64_F64SVD && c->dtype != GMPS_DW)
     return fail(GMPS_ERR_ARG, "unknown dtype");
-  if (c->apply < 0 || c->apply > 2) return fail(GMPS_ERR_ARG, "apply must be 0, 1 or 2");
+  if (c->apply < 0 || c->apply > 3) return fail(GMPS_ERR_ARG, "apply must be 0, 1, 2 or 3");
   if (c->threads != 0 && (c->threads % 32 != 0 || c->threads < 32 || c->threads > 256))
     return fail(GMPS_ERR_ARG, "threads must be a multiple of 32 in [32, 256]");
   if (c->max_sweeps < 0) return fail(GMPS_ERR_ARG, "max_sweeps must be >= 0");
@@ -124,25 +136,34 @@ static gmps_status make_plan_for(const gmps_config* c, bool allow_resident, Plan
   const int slacks[3] = {c->dtype == GMPS_C64_F64SVD ? c->M + 1 : 2, 2, 0};
   for (int si = 0; si < 3; ++si) {
     const int slack = slacks[si];
-    int chicap = std::min(c->chi_max, c->M + 1 + slack);
+    // Grover states have Schmidt rank <= M + 1; gate-level circuits take chi_max
+    int chicap = c->apply == GMPS_APPLY_GATES ? c->chi_max : std::min(c->chi_max, c->M + 1 + slack);
     // a bond never exceeds 2^floor(n/2)
     long long half = 1;
     for (int i = 0; i < c->n / 2 && half < chicap; ++i) half *= 2;
     chicap = (int)std::min<long long>(chicap, half);
     const int xcap = xcap_for(c->apply, c->M, chicap);
-    if (c->apply == GMPS_APPLY_MPO && xcap > 64) continue;
+    const int rcap = rcap_for(c->apply, c->M, chicap, xcap);
     P->chicap = chicap;
     P->xcap = xcap;
+    P->rcap = rcap;
     P->off[0] = 0;
-    for (int l = 0; l < c->n; ++l) P->off[l + 1] = P->off[l] + slot_elems(l, c->n, xcap);
+    for (int l = 0; l < c->n; ++l) P->off[l + 1] = P->off[l] + slot_elems(l, c->n, rcap);
     P->site_elems = P->off[c->n];
     P->elem_bytes = eb;
-    SmemPlan sp = make_plan(c->n, c->M, xcap, chicap, rb, 0);
-    if (sp.total > (size_t)smax) continue;
+    // the QR matrices in shared memory, else in a device work area
+    bool work = false;
+    SmemPlan sp = make_plan(c->n, c->M, xcap, chicap, rcap, rb, 0, false);
+    if (sp.total > (size_t)smax) {
+      sp = make_plan(c->n, c->M, xcap, chicap, rcap, rb, 0, true);
+      if (sp.total > (size_t)smax) continue;
+      work = true;
+    }
+    P->work_bytes = work ? sp.work_bytes : 0;
     P->resident = 0;
     P->smem = sp.total;
     if (allow_resident) {
-      SmemPlan sr = make_plan(c->n, c->M, xcap, chicap, rb, P->site_elems * eb);
+      SmemPlan sr = make_plan(c->n, c->M, xcap, chicap, rcap, rb, P->site_elems * eb, work);
       if (sr.total <= (size_t)smax) {
         P->resident = 1;
         P->smem = sr.total;
@@ -151,17 +172,16 @@ static gmps_status make_plan_for(const gmps_config* c, bool allow_resident, Plan
     P->threads = c->threads ? c->threads : auto_threads(xcap);
     return GMPS_OK;
   }
-  if (c->apply == GMPS_APPLY_MPO)
-    return fail(GMPS_ERR_UNSUPPORTED, "MPO contraction needs (M+1)*chi <= 64; use the direct-sum forms");
   return fail(GMPS_ERR_UNSUPPORTED, "working set exceeds shared memory for this (M, chi_max)");
 }
 
 // ---------------------------------------------------------------- handle
-struct Slab {  // one chain + its descriptor and statistics, carved from an arena
+struct Slab {  // one chain + its descriptor, statistics and work area, carved from an arena
   InstDesc* d_desc = nullptr;
   long long* d_off = nullptr;
   DevStats* d_stats = nullptr;
   void* d_sites = nullptr;
+  void* d_work = nullptr;
 };
 
 struct gmps_ctx {
@@ -206,7 +226,7 @@ struct gmps_ctx {
 
 static size_t slab_bytes(const gmps_config* c, const Plan& P) {
   return a256(sizeof(InstDesc)) + a256(sizeof(long long) * (c->n + 1)) + a256(sizeof(DevStats)) +
-         a256(P.site_elems * P.elem_bytes);
+         a256(P.site_elems * P.elem_bytes) + a256(P.work_bytes);
 }
 
 static char* carve_slab(char* p, const gmps_config* c, const Plan& P, Slab* s) {
@@ -218,6 +238,8 @@ static char* carve_slab(char* p, const gmps_config* c, const Plan& P, Slab* s) {
   p += a256(sizeof(DevStats));
   s->d_sites = p;
   p += a256(P.site_elems * P.elem_bytes);
+  s->d_work = P.work_bytes ? p : nullptr;
+  p += a256(P.work_bytes);
   return p;
 }
 
@@ -235,6 +257,8 @@ static InstDesc base_desc(const gmps_ctx* h, const Slab& s) {
   d.chi_max = h->cfg.chi_max;
   d.chicap = h->plan.chicap;
   d.xcap = h->plan.xcap;
+  d.rcap = h->plan.rcap;
+  d.work = s.d_work;
   d.max_sweeps = h->cfg.max_sweeps ? h->cfg.max_sweeps : kDefaultMaxSweeps;
   d.resident = h->plan.resident;
   d.tol = h->cfg.tol;
@@ -439,6 +463,8 @@ static gmps_status enqueue_iterate(gmps_ctx* h, int64_t k, const double* dphi, c
 
 gmps_status grover_mps_iterate_device(gmps_handle h, int64_t k, const double* dev_phi, const double* dev_psi) {
   if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
+  if (h->cfg.apply == GMPS_APPLY_GATES)
+    return fail(GMPS_ERR_UNSUPPORTED, "a gate-level handle takes circuits (grover_mps_apply_circuit)");
   if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
   if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
   if (k == 0) return GMPS_OK;
@@ -453,6 +479,8 @@ gmps_status grover_mps_iterate_device(gmps_handle h, int64_t k, const double* de
 
 gmps_status grover_mps_iterate(gmps_handle h, int64_t k, const double* host_phi, const double* host_psi) {
   if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
+  if (h->cfg.apply == GMPS_APPLY_GATES)
+    return fail(GMPS_ERR_UNSUPPORTED, "a gate-level handle takes circuits (grover_mps_apply_circuit)");
   if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
   if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
   if (k == 0) return GMPS_OK;
@@ -688,7 +716,7 @@ gmps_status grover_mps_apply_circuit(gmps_handle h, const gmps_gate* gates, int6
   if (!gates) return fail(GMPS_ERR_ARG, "gates is NULL");
   if (h->cfg.differentiable) return fail(GMPS_ERR_UNSUPPORTED, "circuits on differentiable handles are not built");
   if (h->plan.xcap < 2 * h->plan.chicap)
-    return fail(GMPS_ERR_UNSUPPORTED, "circuits need a handle created with apply = GMPS_APPLY_MPO");
+    return fail(GMPS_ERR_UNSUPPORTED, "circuits need a handle created with apply = GMPS_APPLY_GATES or MPO");
   for (int64_t g = 0; g < count; ++g) {
     const gmps_gate& x = gates[g];
     if (x.kind == GMPS_GATE_1Q) {
@@ -860,7 +888,7 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
     }
     const Plan& P = b->plans[i];
     total += a256(sizeof(long long) * (cfgs[i].n + 1)) + a256(sizeof(DevStats)) +
-             a256(P.site_elems * P.elem_bytes) + a256(sizeof(unsigned long long) * cfgs[i].M) +
+             a256(P.site_elems * P.elem_bytes) + a256(P.work_bytes) + a256(sizeof(unsigned long long) * cfgs[i].M) +
              a256(sizeof(double) * 2 * ks[i]);
     smem = std::max(smem, P.smem);
     maxx = std::max(maxx, P.xcap);
@@ -901,6 +929,7 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
     d.chi_max = c.chi_max;
     d.chicap = P.chicap;
     d.xcap = P.xcap;
+    d.rcap = P.rcap;
     d.max_sweeps = c.max_sweeps ? c.max_sweeps : kDefaultMaxSweeps;
     d.resident = 0;
     d.k = ks[i];
@@ -915,6 +944,8 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
     p += a256(sizeof(DevStats));
     d.sites = p;
     p += a256(P.site_elems * P.elem_bytes);
+    d.work = P.work_bytes ? p : nullptr;
+    p += a256(P.work_bytes);
     unsigned long long* mk_ = (unsigned long long*)p;
     p += a256(sizeof(unsigned long long) * c.M);
     d.marked = mk_;
@@ -1129,7 +1160,8 @@ gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int 
                        a256(sizeof(AdjArgs) * 2 * count) + a256(sizeof(DevStats) * nslab) +
                        2 * a256(sizeof(double) * 2 * (size_t)count * K) +
                        a256(sizeof(double) * 2 * (size_t)count * b->every * (M + 1)) +
-                       a256(sizeof(double) * count) + a256(sizeof(int)) + site_b * nslab;
+                       a256(sizeof(double) * count) + a256(sizeof(int)) + site_b * nslab +
+                       a256(b->plan.work_bytes) * 3 * count;
   cudaError_t e = cudaMalloc(&b->mem, bytes);
   if (e != cudaSuccess) {
     grover_mps_diff_batch_destroy(b);
@@ -1150,6 +1182,7 @@ gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int 
   b->d_rec = (double*)p;                      p += a256(sizeof(double) * 2 * (size_t)count * b->every * (M + 1));
   b->d_p = (double*)p;                        p += a256(sizeof(double) * count);
   b->d_queue = (int*)p;                       p += a256(sizeof(int));
+  char* works = p;                            p += a256(b->plan.work_bytes) * 3 * count;
   char* sites = p;
   const RankRule rr = rank_rule_for(cfg->dtype);
   auto desc = [&](int slab) {
@@ -1160,6 +1193,9 @@ gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int 
     d.chi_max = cfg->chi_max;
     d.chicap = b->plan.chicap;
     d.xcap = b->plan.xcap;
+    d.rcap = b->plan.rcap;
+    // main, recompute and costate chains run kernels: each gets a work area
+    d.work = (b->plan.work_bytes && slab < 3 * count) ? works + a256(b->plan.work_bytes) * slab : nullptr;
     d.max_sweeps = cfg->max_sweeps ? cfg->max_sweeps : kDefaultMaxSweeps;
     d.resident = b->plan.resident;
     d.tol = cfg->tol;
@@ -1348,6 +1384,7 @@ extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int
   c.tol = tol;
   gmps_status s = validate(&c);
   if (s) return s;
+  if (apply == GMPS_APPLY_GATES) return fail(GMPS_ERR_UNSUPPORTED, "grover_mps_run_noalloc runs Grover iterations");
   if (!p_marked) return fail(GMPS_ERR_ARG, "p_marked is NULL");
   if (k < 0) return fail(GMPS_ERR_ARG, "k must be >= 0");
   Plan P;
@@ -1361,7 +1398,8 @@ extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int
   const size_t o_marked = o_stats + a256(sizeof(DevStats));
   const size_t o_amp = o_marked + a256(sizeof(uint64_t) * M);
   const size_t o_sites = o_amp + a256(sizeof(double) * 2 * M);
-  const size_t need = o_sites + a256(site_bytes);
+  const size_t o_work = o_sites + a256(site_bytes);
+  const size_t need = o_work + a256(P.work_bytes);
   if (need > kNoAllocScratchBytes)
     return fail(GMPS_ERR_CAPACITY, "instance needs " + std::to_string(need) +
                                        " bytes of static scratch; grover_mps_run_noalloc holds " +
@@ -1378,6 +1416,7 @@ extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int
   d.chi_max = chi_max;
   d.chicap = P.chicap;
   d.xcap = P.xcap;
+  d.rcap = P.rcap;
   d.max_sweeps = kDefaultMaxSweeps;
   d.resident = P.resident;
   d.k = k;
@@ -1390,6 +1429,7 @@ extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int
   d.phi = dev_phi;
   d.psi = dev_psi;
   d.sites = b + o_sites;
+  d.work = P.work_bytes ? (void*)(b + o_work) : nullptr;
   d.site_off = (const long long*)(b + o_off);
   d.stats = (DevStats*)(b + o_stats);
   const InstDesc* d_desc = (const InstDesc*)(b + o_desc);

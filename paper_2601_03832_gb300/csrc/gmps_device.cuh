@@ -944,6 +944,11 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       p = qr_rank_revealing<T>(B.W, m, xr, xr, B.tau, B.beta, B.qperm, B.qcn, B.misc + 8, fl * fl);
     }
     if (p < 1) p = 1;
+    if (p > d.rcap) {  // the rank exceeds what R, W and the slots were sized for
+      if (threadIdx.x == 0) set_status<T>(B.misc, kDevCapacity);
+      __syncthreads();
+      return;
+    }
     // R P^T -> Rp (p x xr, ld xr): column c of the pivoted R is original column perm[c]
     for (int e = threadIdx.x; e < p * xr; e += blockDim.x) {
       const int i = e / xr, c = e % xr;
@@ -1224,7 +1229,7 @@ template <class T, class S>
 __device__ void blk_open(Blk<T, S>& B, const InstDesc& d, unsigned char* smem, bool zero_log_norm) {
   const int n = d.n;
   const size_t site_bytes = d.resident ? (size_t)d.site_off[n] * sizeof(S) : 0;
-  const SmemPlan P = make_plan(n, d.M, d.xcap, d.chicap, sizeof(T), site_bytes);
+  const SmemPlan P = make_plan(n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), site_bytes, d.work != nullptr);
   B.d = &d;
   B.n = n;
   {
@@ -1242,8 +1247,9 @@ __device__ void blk_open(Blk<T, S>& B, const InstDesc& d, unsigned char* smem, b
   B.misc = (int*)(smem + P.off_misc);
   B.dmisc = (double*)(smem + P.off_misc + 128);
   B.tmisc = (T*)(smem + P.off_misc + 256);
-  B.Rp = (cx<T>*)(smem + P.off_rprev);
-  B.W = (cx<T>*)(smem + P.off_w);
+  unsigned char* qbase = d.work ? (unsigned char*)d.work : smem;  // QR matrices
+  B.Rp = (cx<T>*)(qbase + P.off_rprev);
+  B.W = (cx<T>*)(qbase + P.off_w);
   B.tau = (T*)(smem + P.off_tau);
   B.beta = (cx<T>*)(smem + P.off_beta);
   B.Mat = (cx<T>*)(smem + P.off_mat);

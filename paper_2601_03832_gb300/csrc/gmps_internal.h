@@ -43,6 +43,7 @@ struct InstDesc {
   int chi_max;              // user cap
   int chicap;               // storage capacity of a bond after truncation
   int xcap;                 // capacity of an expanded bond
+  int rcap;                 // capacity of a QR-sweep bond (the rank after rank-revealing QR)
   int max_sweeps;
   int resident;             // copy the chain into shared memory for the launch
   long long k;              // iterations to apply in this launch
@@ -57,6 +58,7 @@ struct InstDesc {
   void* sites;              // device slab
   const long long* site_off;  // n+1 offsets (elements of the storage type)
   DevStats* stats;          // device
+  void* work;               // device work area for the QR matrices when they exceed shared memory, else null
   double* rec;              // optional: before each iteration, the marked amplitudes and
                             // <s|psi> of the chain, (M+1) complex per iteration
 };
@@ -79,19 +81,26 @@ struct AdjArgs {
 };
 
 // Shared-memory plan of one block (bytes), identical on host and device.
+// The QR sweep's matrices (R carried along the sweep, rank x expanded bond,
+// and the (2 rank) x expanded-bond work matrix) sit in shared memory, aliased
+// with the SVD sweep's working set, or -- when they do not fit, e.g. a
+// generic MPO with an expanded bond in the thousands -- in a per-instance
+// device work area (work_bytes, offsets from its base).
 struct SmemPlan {
   size_t off_chi, off_qb, off_soff, off_terms, off_amps, off_misc, off_qperm, off_qcn, off_tbuf;
-  size_t off_rprev, off_w, off_tau, off_beta;      // QR sweep
-  size_t off_mat, off_u, off_us, off_sig, off_perm;  // SVD sweep (aliases QR)
+  size_t off_tau, off_beta;                          // QR reflector scalars (shared memory)
+  size_t off_rprev, off_w;                           // QR matrices (shared memory or the work area)
+  size_t off_mat, off_u, off_us, off_sig, off_perm;  // SVD sweep (shared memory)
   size_t off_sites;
-  size_t total;
+  size_t total;       // shared-memory bytes
+  size_t work_bytes;  // work-area bytes, 0 when the QR matrices are in shared memory
 };
 
 GMPS_HD size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // rb = bytes of one real of the linear-algebra type (complex = 2*rb).
-GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, size_t rb,
-                           size_t site_bytes_resident) {
+GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, int rcap, size_t rb,
+                           size_t site_bytes_resident, bool work_global) {
   SmemPlan p{};
   size_t cb = 2 * rb;
   size_t o = 0;
@@ -104,21 +113,22 @@ GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, size_t rb,
   p.off_qperm = o; o = align_up(o + sizeof(int) * (size_t)xcap, 16);   // QR pivots
   p.off_qcn = o;   o = align_up(o + rb * (size_t)xcap, 16);            // QR column norms
   p.off_tbuf = o;  o = align_up(o + (cb * 32 + 16) * 2, 16);           // reflectors handed between warps
-  size_t base = o;
-  // QR-sweep working set
-  size_t q = base;
-  p.off_rprev = q; q = align_up(q + cb * (size_t)xcap * xcap, 16);
-  p.off_w = q;     q = align_up(q + cb * (size_t)(2 * xcap) * xcap, 16);
-  p.off_tau = q;   q = align_up(q + rb * (size_t)xcap, 16);
-  p.off_beta = q;  q = align_up(q + cb * (size_t)xcap, 16);
-  // SVD-sweep working set (aliases the QR one)
+  p.off_tau = o;   o = align_up(o + rb * (size_t)xcap, 16);
+  p.off_beta = o;  o = align_up(o + cb * (size_t)xcap, 16);
+  const size_t base = o;
+  // QR-sweep matrices
+  size_t q = work_global ? 0 : base;
+  p.off_rprev = q; q = align_up(q + cb * (size_t)rcap * xcap, 16);
+  p.off_w = q;     q = align_up(q + cb * (size_t)(2 * rcap) * xcap, 16);
+  p.work_bytes = work_global ? q : 0;
+  // SVD-sweep working set (aliases the QR matrices when those are here)
   size_t s = base;
-  p.off_mat = s;   s = align_up(s + cb * (size_t)xcap * (2 * chicap), 16);
-  p.off_u = s;     s = align_up(s + cb * (size_t)xcap * xcap, 16);          // accumulated rotations
-  p.off_us = s;    s = align_up(s + cb * (size_t)xcap * chicap, 16);
-  p.off_sig = s;   s = align_up(s + rb * (size_t)xcap, 16);
-  p.off_perm = s;  s = align_up(s + sizeof(int) * (size_t)xcap, 16);
-  o = q > s ? q : s;
+  p.off_mat = s;   s = align_up(s + cb * (size_t)rcap * (2 * chicap), 16);
+  p.off_u = s;     s = align_up(s + cb * (size_t)rcap * rcap, 16);         // accumulated rotations
+  p.off_us = s;    s = align_up(s + cb * (size_t)rcap * chicap, 16);
+  p.off_sig = s;   s = align_up(s + rb * (size_t)rcap, 16);
+  p.off_perm = s;  s = align_up(s + sizeof(int) * (size_t)rcap, 16);
+  o = work_global ? s : (q > s ? q : s);
   p.off_sites = o;
   o = align_up(o + site_bytes_resident, 16);
   p.total = o;
@@ -126,16 +136,16 @@ GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, size_t rb,
 }
 
 // Largest left/right dims a slot ever holds: QR-sweep bonds are bounded by
-// 2^l from the left and by the expanded bond xcap.
-GMPS_HD long long bond_cap(int l, int n, int xcap) {
+// 2^l from the left and by the rank capacity rcap.
+GMPS_HD long long bond_cap(int l, int n, int rcap) {
   (void)n;
   long long c = 1;
-  for (int i = 0; i < l && c < xcap; ++i) c *= 2;
-  return c < xcap ? c : xcap;
+  for (int i = 0; i < l && c < rcap; ++i) c *= 2;
+  return c < rcap ? c : rcap;
 }
-GMPS_HD long long slot_elems(int l, int n, int xcap) {
-  long long left = bond_cap(l, n, xcap);
-  long long right = (l == n - 1) ? 1 : bond_cap(l + 1, n, xcap);
+GMPS_HD long long slot_elems(int l, int n, int rcap) {
+  long long left = bond_cap(l, n, rcap);
+  long long right = (l == n - 1) ? 1 : bond_cap(l + 1, n, rcap);
   return left * 2 * right;
 }
 

@@ -20,6 +20,8 @@ single instances for profiling.
 Run: python -m paper_2601_03832_gb300.experiments [--ns 10-29] [--shots-ns 2-29]
      python -m paper_2601_03832_gb300.experiments crossover [--ns 12-31] [--sv-max-iters 400]
      python -m paper_2601_03832_gb300.experiments circuits [--ns 10-29] [--kmax K]
+     python -m paper_2601_03832_gb300.experiments batched [--count 512] [--kcap K] [--dtype c64]
+     python -m paper_2601_03832_gb300.experiments differentiable [--vectors 64]
      python -m paper_2601_03832_gb300.experiments single --n 29 --k 50 [--M 1] [--dtype c128] [--apply fused]
          [--path mps|sv]
 """
@@ -180,6 +182,45 @@ def common_vs_iterative(ns, chi_max=4, kmax=None):
     return rows
 
 
+def batched(count=512, kcap=None, dtype="c64", threads=256):
+    """The batched workload (the first `count` of the 512 instances, k_i
+    capped at kcap) in one persistent launch; returns the wall seconds and
+    the largest |P - closed form| is left to the caller (no reference here)."""
+    import time
+
+    import torch
+    insts = inputs.config_batched(count=512)[:count]
+    if kcap:
+        for i in insts:
+            i.k = min(i.k, kcap)
+    b = binding.GroverBatch(insts, dtype=dtype, apply="fused")
+    b.set_threads(threads)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.run(use_graph=False)
+    p, st, rc = b.result()
+    sec = time.perf_counter() - t0
+    b.close()
+    return {"count": count, "kcap": kcap, "seconds": sec, "iterations": int(sum(i.k for i in insts)),
+            "instances_with_status": int((st != 0).sum()), "P_marked": [float(x) for x in p]}
+
+
+def differentiable(vectors=64):
+    """The differentiable workload (n = 20, M = 4, K = 64, checkpoint every 8)
+    for `vectors` phase vectors through grover_mps_diff_batch_run."""
+    import time
+
+    import torch
+
+    from . import autograd
+    di, phi, psi = inputs.config_differentiable(B=vectors)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L, gphi, gpsi = autograd.loss_and_grad_batch(di.n, di.marked, phi, psi)
+    torch.cuda.synchronize()
+    return {"vectors": vectors, "seconds": time.perf_counter() - t0, "loss": [float(x) for x in L]}
+
+
 def single(n, M, k, dtype="c128", apply="fused", chi_max=None, path="mps", seed=None):
     """One instance (marked strings from seed 1000 + n unless `seed`): k
     iterations on the MPS or statevector path, P_marked printed.  A small,
@@ -218,6 +259,26 @@ def main(argv=None):
         args = ap.parse_args(argv[1:])
         binding.load()
         print(json.dumps({"rows": common_vs_iterative(_range(args.ns), kmax=args.kmax)}))
+        return 0
+    if argv and argv[0] == "batched":
+        ap = argparse.ArgumentParser(description="the batched workload (subset)")
+        ap.add_argument("--count", type=int, default=512)
+        ap.add_argument("--kcap", type=int, default=None)
+        ap.add_argument("--dtype", default="c64")
+        args = ap.parse_args(argv[1:])
+        binding.load()
+        r = batched(args.count, args.kcap, args.dtype)
+        r.pop("P_marked")
+        print(json.dumps(r))
+        return 0
+    if argv and argv[0] == "differentiable":
+        ap = argparse.ArgumentParser(description="the differentiable workload")
+        ap.add_argument("--vectors", type=int, default=64)
+        args = ap.parse_args(argv[1:])
+        binding.load()
+        r = differentiable(args.vectors)
+        r.pop("loss")
+        print(json.dumps(r))
         return 0
     if argv and argv[0] == "single":
         ap = argparse.ArgumentParser(description="one instance")

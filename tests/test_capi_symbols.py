@@ -62,7 +62,7 @@ def test_config_validation_needs_no_gpu():
         (dict(n=5, marked=[3], tol=-1.0), 1, "tol"),
         (dict(n=5, marked=[3], tol=float("nan")), 1, "tol"),
         (dict(n=5, marked=[3], dtype=7), 1, "dtype"),
-        (dict(n=5, marked=[3], apply=3), 1, "apply"),
+        (dict(n=5, marked=[3], apply=4), 1, "apply"),
         (dict(n=5, marked=[3], threads=48), 1, "threads"),
         (dict(n=5, marked=[3], threads=512), 1, "threads"),
         (dict(n=5, marked=[3], max_sweeps=-1), 1, "max_sweeps"),
@@ -89,7 +89,7 @@ def test_noalloc_validation_matches_handle_path_without_gpu():
         (dict(n=5, marked=[40]), 1, "bits >= n"),
         (dict(n=5, marked=[3], chi_max=0), 1, "chi_max"),
         (dict(n=5, marked=[3], tol=float("nan")), 1, "tol"),
-        (dict(n=5, marked=[3], apply=3), 1, "apply"),
+        (dict(n=5, marked=[3], apply=4), 1, "apply"),
         (dict(n=5, marked=[3], k=-1), 1, "k must be"),
     ]
     for kw, status, text in cases:

@@ -73,13 +73,17 @@ def test_random_circuit_against_dense_oracle(B):
     for kind, site, val in ops:
         v = sv.apply_1q(v, n, site, val) if kind == B.GATE_1Q else sv.apply_mcphase(v, val)
     for dtype, tol in (("c128", 1e-11), ("c64", 2e-6)):
-        g = B.GroverMPS(n, [1], dtype=dtype, apply="mpo", chi_max=16)
+        g = B.GroverMPS(n, [1], dtype=dtype, apply="gates", chi_max=16)
         g.apply_circuit(B.make_gates(ops))
         assert np.abs(dense_from_sites(g.export()) - v).max() < tol
 
 
-def test_circuit_needs_mpo_handle(B):
+def test_circuit_needs_mpo_or_gate_handle(B):
     g = B.GroverMPS(10, [5], apply="fused", chi_max=4)
     with pytest.raises(B.GMPSError) as e:
         g.apply_circuit(B.grover_gates(10, [5], 1))
     assert e.value.status == 9
+    h = B.GroverMPS(10, [5], apply="gates", chi_max=8)
+    with pytest.raises(B.GMPSError) as e2:
+        h.iterate(1)
+    assert e2.value.status == 9

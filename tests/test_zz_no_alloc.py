@@ -103,10 +103,9 @@ def test_noalloc_device_phases_and_back_to_back_instances(B):
 
 
 def test_noalloc_accepts_what_the_handle_path_accepts(B):
-    """The planner is shared: an MPO-mode instance that the handle path fits
-    only by dropping the bond headroom (M = 7, chi_max = 16: a bond capacity
-    of M+1+2 = 10 would need (M+1) 10 = 80 > 64 expanded columns, capacity
-    M+1 = 8 fits at 64) runs here too."""
+    """The planner is shared: an MPO-mode instance with M = 7 and
+    chi_max = 16 (expanded bond (M+1) x 10 = 80) plans the same bond capacity
+    on both paths and gives the same bonds."""
     n, M, k = 12, 7, 3
     marked = inputs.marked_strings(n, M, seed=707)
     p_ref, a_ref, chi_ref = _reference(B, n, marked, k, "mpo", 16)
