@@ -33,7 +33,7 @@ SAMPLE_SEED = 2
 # k): DRAM bytes (read + write) per launch, and the FP64 pipe busy share of the
 # SM running the instance (sm__pipe_fp64_cycles_active, summed over its four
 # sub-partitions).  None until a capture of the current kernel is recorded.
-CAPTURE = {"traffic_bytes": None, "fp64_pipe_share": None}
+CAPTURE = {"traffic_bytes": 227584, "fp64_pipe_share": 4 * 0.14789}
 
 
 def flops_per_iter_parts(n: int, chi: int, M: int, apply: str):
@@ -67,19 +67,59 @@ def flops_per_iter_parts(n: int, chi: int, M: int, apply: str):
     return linalg, contr
 
 
+def executed_flops_per_iter(n: int, chi: int, M: int, apply: str) -> float:
+    """Real flops of one iteration as the rank-revealing sweeps execute it at
+    steady state (bond chi at every cut; the iterate stays in span{sum_w |w>,
+    |s>}, so every QR step factors a matrix of 2 chi rows and stops after
+    chi reflectors): per sweep pair with expanded bond X and per site
+      contraction of R (chi rows) into the expanded site: chi x 2 x X chi/.. MACs
+      Householder QR of the 2chi x X matrix, chi reflectors: for step j the
+        X-j-1 trailing columns take a dot, an update (16 flops per element of
+        rows >= j) and a norm update (4 flops)
+      thin Q (2 chi x chi) from the reflectors
+      SVD of the chi x 2 chi matrix (Golub & Van Loan thin-SVD count)
+      absorption of U S into the left neighbour: chi x 2chi x chi MACs.
+    The nominal count below (algorithmic_flops_per_iter) assumes a full-rank
+    QR of the 2X x X expanded matrix instead; for the generic MPO of bond
+    M + 1 (X = (M+1) chi) it exceeds this by orders of magnitude."""
+    if apply == "fused":
+        ops = [(chi + M + 1, chi * chi + M + 1)]
+    elif apply == "split":
+        ops = [(chi + M, chi * chi + M), (chi + 1, chi * chi + 1)]
+    else:
+        ops = [((M + 1) * chi, (M + 1) * chi * chi), (2 * chi, 2 * chi * chi)]
+    total = 0.0
+    for X, macs_per_row in ops:
+        m, p = 2 * chi, chi
+        qr = sum((X - j - 1) * (m - j) * 20 for j in range(p))
+        q = sum((p - j - 1) * (m - j) * 16 + 8 * (m - j) for j in range(p))
+        svd = 4 * (14 * (2 * chi) * chi ** 2 + 8 * chi ** 3)
+        contr = 8 * chi * 2 * macs_per_row + 8 * chi * 2 * chi * chi
+        total += (n - 1) * (qr + q + svd + contr)
+    return total
+
+
 def algorithmic_flops_per_iter(n: int, chi: int, M: int, apply: str) -> float:
     """Total algorithmic real flops of one iteration (flops_per_iter_parts summed)."""
     a, b = flops_per_iter_parts(n, chi, M, apply)
     return a + b
 
 
-def roofline_alu(flops: float, seconds: float, peak_tflops: float, peak_name: str, sms_used: int, sms: int):
-    """ALU roofline entry: achieved algorithmic TFLOP/s against the measured
-    chip peak, and against the share of it that the SMs the work ran on hold."""
+def roofline_alu(flops: float, seconds: float, peak_tflops: float, peak_name: str, sms_used: int, sms: int,
+                 nominal_flops: float = None):
+    """ALU roofline entry: achieved TFLOP/s (flops: the executed count of
+    executed_flops_per_iter) against the measured chip peak, and against the
+    share of it that the SMs the work ran on hold; with nominal_flops, the
+    same time against the nominal full-rank count beside it."""
     ach = flops / seconds / 1e12
-    return {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
-            "peak_source": f"measured {peak_name} (libgmps_peaks.so, this run)",
-            "sms_used": sms_used, "frac_of_sms_used": ach / (peak_tflops * sms_used / sms)}
+    out = {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach / peak_tflops,
+           "peak_source": f"measured {peak_name} (libgmps_peaks.so, this run)",
+           "sms_used": sms_used, "frac_of_sms_used": ach / (peak_tflops * sms_used / sms),
+           "flop_model": "executed (rank-revealing QR on 2 chi rows, chi reflectors; thin SVD of chi x 2 chi)"}
+    if nominal_flops is not None:
+        out["nominal"] = {"flops": nominal_flops, "achieved": nominal_flops / seconds / 1e12,
+                          "model": "full-rank QR of the 2X x X expanded matrix (Golub-Van Loan counts)"}
+    return out
 
 
 class ClockSampler:
@@ -240,7 +280,7 @@ def extra_workloads(B, inputs, sptr, peaks):
     sec, _ = timed(lambda: bt.run(use_graph=True))
     p, st, rc = bt.result()
     errs, rel = [], []
-    flops = 0.0
+    flops = nflops = 0.0
     busy, t0s, t1s, longest = {}, [], [], 0.0
     bad_bonds = 0
     for i, x in enumerate(insts):
@@ -248,7 +288,8 @@ def extra_workloads(B, inputs, sptr, peaks):
         errs.append(abs(p[i] - P))
         rel.append(abs(p[i] - P) / P)
         s_ = bt.stats(i)
-        flops += x.k * algorithmic_flops_per_iter(x.n, s_["max_bond"], x.M, APPLY)
+        flops += x.k * executed_flops_per_iter(x.n, s_["max_bond"], x.M, APPLY)
+        nflops += x.k * algorithmic_flops_per_iter(x.n, s_["max_bond"], x.M, APPLY)
         d = (s_["t_end_ns"] - s_["t_begin_ns"]) / 1e9
         busy[s_["sm_id"]] = busy.get(s_["sm_id"], 0.0) + d
         t0s.append(s_["t_begin_ns"])
@@ -258,7 +299,7 @@ def extra_workloads(B, inputs, sptr, peaks):
             bad_bonds += 1
     span = (max(t1s) - min(t0s)) / 1e9
     tot = sum(x.k for x in insts)
-    rl = roofline_alu(flops, sec, fp64, "FP64 FMA", sms, sms)
+    rl = roofline_alu(flops, sec, fp64, "FP64 FMA", sms, sms, nflops)
     out["batched_512_c64"] = {
         "iterations_per_s": tot / sec, "seconds": sec, "total_iterations": tot,
         "k": "full, min(floor(pi/4 sqrt(2^n/M)), 4000)", "threads": thr, "autotune": rec, "graph": True,
@@ -281,8 +322,30 @@ def extra_workloads(B, inputs, sptr, peaks):
     chi = g.stats()["max_bond"]
     out["n40_M32_c128"] = {"iterations_per_s": mi.k / sec, "k": mi.k, "seconds": sec, "P_marked": p,
                            "P_closed_form": Pm, "P_rel_err": (p - Pm) / Pm, "max_bond": chi,
-                           "roofline": roofline_alu(mi.k * algorithmic_flops_per_iter(mi.n, chi, mi.M, APPLY),
-                                                    sec, fp64, "FP64 FMA", 1, sms)}
+                           "roofline": roofline_alu(mi.k * executed_flops_per_iter(mi.n, chi, mi.M, APPLY),
+                                                    sec, fp64, "FP64 FMA", 1, sms,
+                                                    mi.k * algorithmic_flops_per_iter(mi.n, chi, mi.M, APPLY))}
+    g.close()
+    # the same instance with the oracle as a generic MPO of bond M + 1 = 33
+    # (expanded bond 33 x 35 = 1155; QR matrices in the device work area),
+    # a k = 5 slice
+    mg = inputs.config_multi_marked(k=5)
+    g = B.GroverMPS(mg.n, mg.marked, dtype="c128", apply="mpo", chi_max=mg.chi_max, tol=mg.tol, stream=sptr)
+    g.iterate(1)                                                   # warm-up iteration
+    g.reset()
+    sec, _ = timed(lambda: g.iterate(mg.k))
+    p = g.prob_marked()
+    Pm = reduced.closed_form(mg.n, mg.M, mg.k)[0]
+    gst = g.stats()
+    chi = gst["max_bond"]
+    # QR at the expanded bond X = (M+1) chi_l for the oracle, 2 chi_l for the
+    # diffusion, on matrices of 2 r_l rows with r_l <= chi + M the rank the
+    # QR reveals; SVD at the kept bonds
+    out["n40_M32_generic_mpo_c128"] = {
+        "iterations_per_s": mg.k / sec, "k_slice": mg.k, "seconds": sec, "P_rel_err": (p - Pm) / Pm, "max_bond": chi,
+        "expanded_bond": (mg.M + 1) * 35, "ctas": gst["ctas"],
+        "roofline": roofline_alu(mg.k * executed_flops_per_iter(mg.n, chi, mg.M, "mpo"), sec, fp64, "FP64 FMA",
+                                 gst["ctas"], sms, mg.k * algorithmic_flops_per_iter(mg.n, chi, mg.M, "mpo"))}
     g.close()
     # differentiable: n = 20, M = 4, K = 64, the batch of 64 phase vectors,
     # forward + backward of all 64
@@ -299,11 +362,12 @@ def extra_workloads(B, inputs, sptr, peaks):
         L, rphi, rpsi = reduced.loss_and_grad(di.n, di.M, phi[b], psi[b])
         worst = max(worst, abs(Ls[b] - L), float(np.abs(gphis[b] - rphi).max()), float(np.abs(gpsis[b] - rpsi).max()))
     # forward K iterations, segment recompute K iterations, costate K steps
-    dflops = len(phi) * 3 * di.k * algorithmic_flops_per_iter(di.n, di.M + 1, di.M, APPLY)
+    dflops = len(phi) * 3 * di.k * executed_flops_per_iter(di.n, di.M + 1, di.M, APPLY)
+    dnom = len(phi) * 3 * di.k * algorithmic_flops_per_iter(di.n, di.M + 1, di.M, APPLY)
     out["differentiable_n20_M4_K64"] = {"fwd_bwd_ms_per_vector": 1000 * sec / len(phi), "vectors": len(phi),
                                         "wall_s": sec, "max_err_vs_reduced_model": worst,
                                         "roofline": roofline_alu(dflops, sec, fp64, "FP64 FMA",
-                                                                 min(len(phi), sms), sms)}
+                                                                 min(len(phi), sms), sms, dnom)}
     return out
 
 
@@ -428,9 +492,10 @@ def main():
     Pc, awc, arc = reduced.closed_form(inst.n, inst.M, k)
     st = g.stats()
     chi = max(st["chi"])
-    flops = k * algorithmic_flops_per_iter(inst.n, chi, inst.M, APPLY)
+    flops = k * executed_flops_per_iter(inst.n, chi, inst.M, APPLY)
     kern_s = statistics.mean(kern_ms) / 1000.0
-    roof = roofline_alu(flops, kern_s, peaks["fp64_fma_tflops"], "FP64 FMA", 1, peaks["sms"])
+    roof = roofline_alu(flops, kern_s, peaks["fp64_fma_tflops"], "FP64 FMA", 1, peaks["sms"],
+                        k * algorithmic_flops_per_iter(inst.n, chi, inst.M, APPLY))
     roof.update({"traffic": CAPTURE["traffic_bytes"], "kernel": "iterate_kernel<double,double2,double>",
                  "algorithmic_flops_per_launch": flops, "kernel_ms": statistics.mean(kern_ms)})
     if CAPTURE["fp64_pipe_share"] is not None:

@@ -126,6 +126,10 @@ typedef struct gmps_stats {
   int sm_id;                /* SM that ran the instance's last iterate launch */
   int64_t t_begin_ns;       /* device clock (ns) when that launch began ... */
   int64_t t_end_ns;         /* ... and finished this instance */
+  int ctas;                 /* CTAs (one SM each) that run one iterate launch of
+                               the instance: 1, or the thread-block cluster whose
+                               CTAs share the QR steps of a generic MPO with an
+                               expanded bond of 256 or more (FP64, complex64) */
 } gmps_stats;
 
 /* ------------------------------------------------------------------ */

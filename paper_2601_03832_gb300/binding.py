@@ -61,7 +61,7 @@ class gmps_stats(C.Structure):
                 ("log_norm", C.c_double), ("discarded_weight", C.c_double),
                 ("max_jacobi_sweeps", C.c_int), ("jacobi_sweeps", C.c_int64), ("svd_count", C.c_int64),
                 ("device_status", C.c_int), ("sm_id", C.c_int), ("t_begin_ns", C.c_int64),
-                ("t_end_ns", C.c_int64)]
+                ("t_end_ns", C.c_int64), ("ctas", C.c_int)]
 
 
 def _stats_dict(s, n):
@@ -69,7 +69,7 @@ def _stats_dict(s, n):
             "log_norm": s.log_norm, "discarded_weight": s.discarded_weight,
             "max_jacobi_sweeps": s.max_jacobi_sweeps, "jacobi_sweeps": s.jacobi_sweeps,
             "svd_count": s.svd_count, "device_status": s.device_status, "sm_id": s.sm_id,
-            "t_begin_ns": s.t_begin_ns, "t_end_ns": s.t_end_ns}
+            "t_begin_ns": s.t_begin_ns, "t_end_ns": s.t_end_ns, "ctas": s.ctas}
 
 
 class GMPSError(RuntimeError):

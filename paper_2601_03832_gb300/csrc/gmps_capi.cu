@@ -71,6 +71,7 @@ static RankRule rank_rule_for(int dtype) {
 // planning allocates nothing).
 struct Plan {
   int chicap, xcap, rcap, threads, resident;
+  int cluster;               // CTAs sharing a single instance's large QR steps (1: none)
   size_t smem, site_elems, elem_bytes;
   size_t work_bytes;         // device work area for the QR matrices (0: in shared memory)
   long long off[kMaxN + 1];  // slot offsets, n+1 used
@@ -160,6 +161,9 @@ static gmps_status make_plan_for(const gmps_config* c, bool allow_resident, Plan
       work = true;
     }
     P->work_bytes = work ? sp.work_bytes : 0;
+    // a generic MPO with an expanded bond in the hundreds: its QR steps are
+    // split over a cluster of CTAs when the instance runs alone (FP64 QR)
+    P->cluster = (work && c->apply == GMPS_APPLY_MPO && c->dtype != GMPS_DW && xcap >= kClusterMinCols) ? kMaxCluster : 1;
     P->resident = 0;
     P->smem = sp.total;
     if (allow_resident) {
@@ -259,6 +263,7 @@ static InstDesc base_desc(const gmps_ctx* h, const Slab& s) {
   d.xcap = h->plan.xcap;
   d.rcap = h->plan.rcap;
   d.work = s.d_work;
+  d.cluster = h->plan.cluster;
   d.max_sweeps = h->cfg.max_sweeps ? h->cfg.max_sweeps : kDefaultMaxSweeps;
   d.resident = h->plan.resident;
   d.tol = h->cfg.tol;
@@ -457,7 +462,8 @@ static gmps_status enqueue_iterate(gmps_ctx* h, int64_t k, const double* dphi, c
   d.psi = dpsi;
   d.rec = rec;
   CUDA_TRY(cudaMemcpyAsync(slab.d_desc, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(launch_iterate(slab.d_desc, 1, nullptr, h->cfg.dtype, h->plan.threads, h->plan.smem, 1, h->stream));
+  CUDA_TRY(launch_iterate(slab.d_desc, 1, nullptr, h->cfg.dtype, h->plan.threads, h->plan.smem, 1, h->stream,
+                          h->plan.cluster));
   return GMPS_OK;
 }
 
@@ -594,7 +600,7 @@ gmps_status grover_mps_sample(gmps_handle h, int64_t shots, uint64_t seed, uint6
   return check_device(h);
 }
 
-static void fill_stats(const DevStats& ds, int n, gmps_stats* out) {
+static void fill_stats(const DevStats& ds, int n, int ctas, gmps_stats* out) {
   memset(out, 0, sizeof(*out));
   out->iterations = ds.iterations;
   out->n = n;
@@ -613,6 +619,7 @@ static void fill_stats(const DevStats& ds, int n, gmps_stats* out) {
   out->sm_id = ds.sm;
   out->t_begin_ns = (int64_t)ds.t_begin;
   out->t_end_ns = (int64_t)ds.t_end;
+  out->ctas = ctas;
 }
 
 gmps_status grover_mps_stats(gmps_handle h, gmps_stats* out) {
@@ -620,7 +627,7 @@ gmps_status grover_mps_stats(gmps_handle h, gmps_stats* out) {
   DevStats ds;
   CUDA_TRY(cudaMemcpyAsync(&ds, h->main.d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  fill_stats(ds, h->cfg.n, out);
+  fill_stats(ds, h->cfg.n, std::max(1, h->plan.cluster), out);
   return GMPS_OK;
 }
 
@@ -1063,7 +1070,7 @@ gmps_status grover_mps_batch_stats(gmps_batch_handle b, int i, gmps_stats* out) 
   DevStats ds;
   CUDA_TRY(cudaMemcpyAsync(&ds, b->h[q].stats, sizeof(DevStats), cudaMemcpyDeviceToHost, b->stream));
   CUDA_TRY(cudaStreamSynchronize(b->stream));
-  fill_stats(ds, b->cfgs[i].n, out);
+  fill_stats(ds, b->cfgs[i].n, 1, out);
   return GMPS_OK;
 }
 
@@ -1440,7 +1447,7 @@ extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int
   CUDA_TRY(cudaMemcpyAsync(b + o_off, P.off, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, stream));
   CUDA_TRY(cudaMemcpyAsync(b + o_marked, marked, sizeof(uint64_t) * M, cudaMemcpyHostToDevice, stream));
   CUDA_TRY(launch_init(d_desc, 1, GMPS_C128, 64, stream));  // statistics and the |+>^n chain
-  if (k > 0) CUDA_TRY(launch_iterate(d_desc, 1, nullptr, GMPS_C128, P.threads, P.smem, 1, stream));
+  if (k > 0) CUDA_TRY(launch_iterate(d_desc, 1, nullptr, GMPS_C128, P.threads, P.smem, 1, stream, P.cluster));
   CUDA_TRY(launch_amplitudes(d_desc, 0, GMPS_C128, (const unsigned long long*)(b + o_marked), M, d_amp, stream));
   double amps[2 * kMaxMarked];
   DevStats ds;

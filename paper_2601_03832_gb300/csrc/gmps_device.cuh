@@ -25,7 +25,13 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
 #include "gmps_forms.h"
+
+namespace cg = cooperative_groups;
 
 namespace gmps {
 
@@ -268,6 +274,7 @@ struct Blk {
   int* misc;               // [0] status, [1] max sweeps, [2] sweeps sum, [3] svd count, [4] k kept
   double* dmisc;           // [0] log_norm, [1] discarded, [2..5] phase coefficients
   unsigned long long rng;  // key of this sweep pair's stochastic rounding (complex64 storage)
+  int csize;               // CTAs of the cluster sharing the large QR steps (1: this block alone)
   T* tmisc;                // [0] rank-rule eps, [1] tol, [2] discarded weight, [3..6] e^{i phi}-1 and 1-e^{i psi},
                            // [7] 2^{-n/2}, [8] Jacobi skip floor, [9] squared norm of the swept matrices
   __device__ S* slot(int l) const { return sites + off[l]; }
@@ -479,6 +486,266 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
     __syncthreads();
   }
   return rank;
+}
+
+// ------------------------------------------------------ QR over a cluster
+// A large rank-revealing QR (a generic MPO's expanded bond in the hundreds or
+// thousands of columns) split over the CTAs of a thread-block cluster: CTA r
+// owns a contiguous slice of the columns of the work matrix W (global memory,
+// m x ncol), keeps their norms in its shared memory and updates them; the
+// pivot choice and the pivot's Householder reflector are exchanged through the
+// instance's work area.  Per reflector step: every CTA posts its best column,
+// a cluster barrier, every CTA picks the same global best (largest norm,
+// lowest column on ties) and the same stop decision; the owner builds the
+// reflector into refl[:, j]; a cluster barrier; every CTA applies it to its
+// remaining columns.  Columns are not swapped: R comes out in the original
+// column order (R P^T), as the single-CTA routine leaves it in Rp.  All loop
+// counts are decided from data every CTA reads after the same barrier, so the
+// CTAs always meet the same barriers.  Returns the rank, or maxrank + 1 when
+// the columns left after maxrank reflectors are still above the floor.
+struct ClusterCand {
+  float key;   // FP32 image of the squared column norm (-1: no column left)
+  int col;
+  double val;  // the squared norm
+};
+struct ClusterCtl {
+  int op;      // 0: exit, 1: QR of the work matrix
+  int m, ncol;
+  int pad;
+  double floor_rel2;
+  double pad2[3];
+  ClusterCand cand[kMaxCluster];
+};
+static_assert(sizeof(ClusterCtl) <= kClusterCtlBytes, "cluster control block");
+
+template <class T>
+struct ClusterView {
+  ClusterCtl* c;
+  int* piv;       // column pivoted at step j
+  T* tau;
+  cx<T>* beta;
+};
+template <class T>
+__device__ __forceinline__ ClusterView<T> cluster_view(unsigned char* work, const SmemPlan& P, int rcap) {
+  unsigned char* b = work + P.off_ctl;
+  ClusterView<T> v;
+  v.c = (ClusterCtl*)b;
+  b += kClusterCtlBytes;
+  v.piv = (int*)b;
+  b += align_up(sizeof(int) * (size_t)rcap, 16);
+  v.tau = (T*)b;
+  b += align_up(sizeof(T) * (size_t)rcap, 16);
+  v.beta = (cx<T>*)b;
+  return v;
+}
+
+// complex load that bypasses L1 (written by another CTA of the cluster)
+__device__ __forceinline__ cx<double> ldcg_cx(const cx<double>* p) {
+  const double2 v = __ldcg((const double2*)p);
+  return mk<double>(v.x, v.y);
+}
+
+template <class T>
+__device__ int cluster_qr(cx<T>* W, int m, int ncol, cx<T>* Rp, cx<T>* refl, int ldr, const ClusterView<T>& cv,
+                          T floor_rel2, int maxrank, T* cn, int* pstep) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
+  const int per = (ncol + csize - 1) / csize;
+  const int c0 = min(ncol, crank * per), c1 = min(ncol, c0 + per);
+  const int nloc = c1 - c0;
+  const int pmax = min(m, ncol);
+  const int G = pow2_cap32(m);
+  const Grp g = make_grp(G);
+  for (int t0 = 0; t0 < nloc; t0 += g.ng) {
+    const int lc = t0 + g.gid;
+    T s2 = 0;
+    if (lc < nloc)
+      for (int i = g.lg; i < m; i += G) s2 += abs2(W[i * ncol + c0 + lc]);
+    s2 = gsum(s2, G);
+    if (lc < nloc && g.lg == 0) {
+      cn[lc] = s2;
+      pstep[lc] = -1;
+    }
+  }
+  __syncthreads();
+  T floor2 = 0;
+  int rank = pmax;
+  for (int j = 0; j < pmax; ++j) {
+    if (threadIdx.x == 0) {
+      int best = -1;
+      float bv = -1.f;
+      for (int lc = 0; lc < nloc; ++lc) {
+        if (pstep[lc] >= 0) continue;
+        const float v = f32_scaled(cn[lc], 0);
+        if (v > bv) {
+          bv = v;
+          best = lc;
+        }
+      }
+      cv.c->cand[crank].key = bv;
+      cv.c->cand[crank].col = best < 0 ? -1 : c0 + best;
+      cv.c->cand[crank].val = best < 0 ? 0.0 : (double)cn[best];
+      __threadfence();
+    }
+    cl.sync();  // candidates posted
+    float bk = -1.f;
+    int bc = -1;
+    double bval = 0.0;
+    for (int r = 0; r < csize; ++r) {
+      const float k = __ldcg(&cv.c->cand[r].key);
+      const int col = __ldcg(&cv.c->cand[r].col);
+      if (col >= 0 && (k > bk || (k == bk && col < bc))) {
+        bk = k;
+        bc = col;
+        bval = __ldcg(&cv.c->cand[r].val);
+      }
+    }
+    if (j == 0) floor2 = (T)bval * floor_rel2;
+    if (bc < 0 || (j > 0 && !((T)bval > floor2))) {
+      rank = j;
+      break;
+    }
+    if (j == maxrank) {  // a further direction above the floor: capacity exceeded
+      rank = maxrank + 1;
+      break;
+    }
+    const bool mine = bc >= c0 && bc < c1;
+    if (mine) {
+      if (threadIdx.x == 0) {
+        // H = I - tau v v^dag with v = x - beta e_j, beta = -e^{i arg x_j} |x|
+        const T s = cn[bc - c0];
+        const cx<T> x0 = W[j * ncol + bc];
+        const T a2 = abs2(x0);
+        cx<T> b = mk<T>(0, 0);
+        T t = 0;
+        if (s > K<T>::tiny2()) {
+          const T inv = rsqrt(s);
+          const T nrm = s * inv;
+          cx<T> ph = mk<T>(1, 0);
+          T ax0 = 0;
+          if (a2 > K<T>::phase_floor() * s) {
+            const T ia = rsqrt(a2);
+            ax0 = a2 * ia;
+            ph = cscale(x0, ia);
+          }
+          b = cscale(ph, -nrm);
+          t = (T)1 / (nrm * (nrm + ax0));
+          W[j * ncol + bc] = csub(x0, b);
+        }
+        cv.tau[j] = t;
+        cv.beta[j] = b;
+        cv.piv[j] = bc;
+        pstep[bc - c0] = j;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) refl[i * ldr + j] = i < j ? mk<T>(0, 0) : W[i * ncol + bc];
+      __threadfence();
+    }
+    cl.sync();  // reflector j posted
+    const T tj = __ldcg(&cv.tau[j]);
+    for (int t0 = 0; t0 < nloc; t0 += g.ng) {
+      const int lc = t0 + g.gid;
+      const bool act = lc < nloc && pstep[lc] < 0;
+      const int c = c0 + lc;
+      cx<T> w = mk<T>(0, 0);
+      if (act)
+        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, ldcg_cx(refl + i * ldr + j), W[i * ncol + c]);
+      w.re = gsum(w.re, G);
+      w.im = gsum(w.im, G);
+      T s2 = 0;
+      if (act) {
+        const cx<T> tw = cscale(w, -tj);
+        for (int i = j + g.lg; i < m; i += G) {
+          cx<T> x = W[i * ncol + c];
+          if (tj != (T)0) x = cmac(x, ldcg_cx(refl + i * ldr + j), tw);
+          W[i * ncol + c] = x;
+          if (i > j) s2 += abs2(x);
+        }
+      }
+      s2 = gsum(s2, G);
+      if (act && g.lg == 0) cn[lc] = s2;
+    }
+    __syncthreads();
+  }
+  // R P^T into Rp (rows < rank, this CTA's columns): a column pivoted at step
+  // i' holds R above row i', beta at row i' and its reflector below
+  const int rows = min(rank, maxrank);
+  for (int e = threadIdx.x; e < rows * nloc; e += blockDim.x) {
+    const int i = e / nloc, lc = e % nloc, c = c0 + lc;
+    const int ps = pstep[lc];
+    cx<T> v;
+    if (ps < 0 || i < ps)
+      v = W[i * ncol + c];
+    else if (i == ps)
+      v = ldcg_cx(&cv.beta[i]);
+    else
+      v = mk<T>(0, 0);
+    Rp[i * ncol + c] = v;
+  }
+  __threadfence();
+  cl.sync();  // R and the reflectors complete
+  return rank;
+}
+
+// A cluster CTA other than the first: waits for the first CTA's commands and
+// takes its share of each large QR until told to stop.
+template <class T>
+__device__ void cluster_worker(const InstDesc& d, unsigned char* smem) {
+  cg::cluster_group cl = cg::this_cluster();
+  const SmemPlan P = make_plan(d.n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), 0, true);
+  unsigned char* work = (unsigned char*)d.work;
+  const ClusterView<T> cv = cluster_view<T>(work, P, d.rcap);
+  T* cn = (T*)smem;
+  int* pstep = (int*)(smem + align_up(sizeof(T) * (size_t)d.xcap, 16));
+  for (;;) {
+    cl.sync();  // a command is posted
+    if (__ldcg(&cv.c->op) == 0) break;
+    const int m = __ldcg(&cv.c->m), ncol = __ldcg(&cv.c->ncol);
+    const T fl2 = (T)__ldcg(&cv.c->floor_rel2);
+    cluster_qr<T>((cx<T>*)(work + P.off_w), m, ncol, (cx<T>*)(work + P.off_rprev), (cx<T>*)(work + P.off_refl),
+                  d.rcap, cv, fl2, d.rcap, cn, pstep);
+  }
+}
+
+// qr_form_q for reflectors that other CTAs of the cluster wrote (A in global
+// memory): every read of A bypasses L1.
+__device__ inline void qr_form_q_cluster(cx<double>* A, int m, int p, int lda, const double* tau) {
+  const int G = pow2_cap32(m);
+  const Grp g = make_grp(G);
+  for (int j = p - 1; j >= 0; --j) {
+    const double tj = tau[j];
+    const int ntask = p - j - 1;
+    for (int t0 = 0; t0 < ntask; t0 += g.ng) {
+      const int c = j + 1 + t0 + g.gid;
+      const bool act = (t0 + g.gid) < ntask;
+      cx<double> w = mk<double>(0, 0);
+      if (act)
+        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, ldcg_cx(A + i * lda + j), ldcg_cx(A + i * lda + c));
+      w.re = gsum(w.re, G);
+      w.im = gsum(w.im, G);
+      if (act && tj != 0.0) {
+        const cx<double> tw = cscale(w, -tj);
+        for (int i = j + g.lg; i < m; i += G) A[i * lda + c] = cmac(ldcg_cx(A + i * lda + c), ldcg_cx(A + i * lda + j), tw);
+      }
+    }
+    __syncthreads();
+    const cx<double> vj = ldcg_cx(A + j * lda + j);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      cx<double> q;
+      if (i < j) {
+        q = mk<double>(0, 0);
+      } else if (i == j) {
+        q = mk<double>(1.0 - tj * abs2(vj), 0);
+      } else {
+        const cx<double> vi = ldcg_cx(A + i * lda + j);
+        q = mk<double>(-tj * fma(vi.re, vj.re, vi.im * vj.im), -tj * fma(vi.im, vj.re, -vi.re * vj.im));
+      }
+      A[i * lda + j] = q;
+    }
+    __threadfence_block();
+    __syncthreads();
+  }
 }
 
 // Overwrite the reflectors in A (m x p block, leading dim lda) with the thin
@@ -939,6 +1206,41 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       break;
     }
     int p;
+    if constexpr (std::is_same<T, double>::value) {
+      if (B.csize > 1 && xr >= kClusterMinCols && d.work != nullptr) {
+        // the whole cluster factors W: post the command, share the columns
+        const SmemPlan Pw = make_plan(n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), 0, true);
+        unsigned char* work = (unsigned char*)d.work;
+        const ClusterView<T> cv = cluster_view<T>(work, Pw, d.rcap);
+        const T fl = rank_floor(B, m, xr);
+        if (threadIdx.x == 0) {
+          cv.c->op = 1;
+          cv.c->m = m;
+          cv.c->ncol = xr;
+          cv.c->floor_rel2 = (double)(fl * fl);
+          __threadfence();
+        }
+        __syncthreads();
+        cg::this_cluster().sync();  // command posted
+        cx<T>* refl = (cx<T>*)(work + Pw.off_refl);
+        p = cluster_qr<T>(B.W, m, xr, B.Rp, refl, d.rcap, cv, fl * fl, d.rcap, B.qcn, B.qperm);
+        if (p < 1) p = 1;
+        if (p > d.rcap) {
+          if (threadIdx.x == 0) set_status<T>(B.misc, kDevCapacity);
+          __syncthreads();
+          return;
+        }
+        for (int j = threadIdx.x; j < p; j += blockDim.x) B.tau[j] = __ldcg(&cv.tau[j]);
+        __syncthreads();
+        qr_form_q_cluster(refl, m, p, d.rcap, B.tau);
+        for (int e = threadIdx.x; e < m * p; e += blockDim.x)
+          st_site(dst + e, ldcg_cx(refl + (e / p) * d.rcap + (e % p)), B.key(l, 0), e);
+        if (threadIdx.x == 0) B.qb[l + 1] = p;
+        __syncthreads();
+        r = p;
+        continue;
+      }
+    }
     {
       const T fl = rank_floor(B, m, xr);
       p = qr_rank_revealing<T>(B.W, m, xr, xr, B.tau, B.beta, B.qperm, B.qcn, B.misc + 8, fl * fl);
@@ -1232,6 +1534,7 @@ __device__ void blk_open(Blk<T, S>& B, const InstDesc& d, unsigned char* smem, b
   const SmemPlan P = make_plan(n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), site_bytes, d.work != nullptr);
   B.d = &d;
   B.n = n;
+  B.csize = 1;
   {
     int* so = (int*)(smem + P.off_soff);
     for (int l = threadIdx.x; l <= n; l += blockDim.x) so[l] = (int)d.site_off[l];
@@ -1312,6 +1615,15 @@ template <class T, class S, class CR>
 __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int count, int* queue) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_idx;
+  // a single instance may run on a cluster: the first CTA runs the sweeps,
+  // the others take shares of its large QR steps (cluster_worker)
+  const int csize = count == 1 ? (int)cg::this_cluster().num_blocks() : 1;
+  if constexpr (std::is_same<T, double>::value) {
+    if (csize > 1 && cg::this_cluster().block_rank() != 0) {
+      cluster_worker<T>(descs[0], smem);
+      return;
+    }
+  }
   for (;;) {
     if (threadIdx.x == 0) s_idx = (count == 1) ? (blockIdx.x == 0 ? 0 : count) : atomicAdd(queue, 1);
     __syncthreads();
@@ -1325,6 +1637,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
     Blk<T, S> B;
     B.rng = 0;
     blk_open(B, d, smem, false);
+    B.csize = csize;
     DevStats* ds = d.stats;
     const int M = d.M;
     long long done = 0;
@@ -1442,6 +1755,19 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
     }
     __syncthreads();
     if (count == 1) break;
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    if (csize > 1) {  // release the cluster's other CTAs
+      const InstDesc& d = descs[0];
+      const SmemPlan Pw = make_plan(d.n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), 0, true);
+      const ClusterView<T> cv = cluster_view<T>((unsigned char*)d.work, Pw, d.rcap);
+      if (threadIdx.x == 0) {
+        cv.c->op = 0;
+        __threadfence();
+      }
+      __syncthreads();
+      cg::this_cluster().sync();
+    }
   }
 }
 
@@ -1885,11 +2211,29 @@ cudaError_t FormLaunch<T, S, CR>::init(const InstDesc* d_desc, int count, cudaSt
 
 template <class T, class S, class CR>
 cudaError_t FormLaunch<T, S, CR>::iterate(const InstDesc* d_desc, int count, int* d_queue, int threads, size_t smem,
-                                          int grid, cudaStream_t stream) {
+                                          int grid, cudaStream_t stream, int cluster) {
   auto k = iterate_kernel<T, S, CR>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<grid, threads, smem, stream>>>(d_desc, count, d_queue);
+  if (cluster > 1 && count == 1 && std::is_same<T, double>::value) {
+    // one instance on a cluster of `cluster` CTAs (one per SM)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k, d_desc, count, d_queue);
+    if (e != cudaSuccess) return e;
+  } else {
+    k<<<grid, threads, smem, stream>>>(d_desc, count, d_queue);
+  }
   count_launch(1);
   return cudaGetLastError();
 }

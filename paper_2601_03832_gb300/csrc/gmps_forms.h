@@ -16,7 +16,7 @@ template <class T, class S, class CR>
 struct FormLaunch {
   static cudaError_t init(const InstDesc* d_desc, int count, cudaStream_t stream);
   static cudaError_t iterate(const InstDesc* d_desc, int count, int* d_queue, int threads, size_t smem, int grid,
-                             cudaStream_t stream);
+                             cudaStream_t stream, int cluster);
   static cudaError_t adjoint(const InstDesc* d_mu, const AdjArgs* d_args, int count, int threads, size_t smem,
                              long long k_lo, long long k_hi, int project, cudaStream_t stream);
   static cudaError_t amplitudes(const InstDesc* d_desc, int inst, const unsigned long long* d_bits, int nbits,

@@ -12,6 +12,9 @@ namespace gmps {
 constexpr int kMaxN = 64;
 constexpr int kMaxMarked = 64;        // direct-sum terms per operator
 constexpr int kDefaultMaxSweeps = 40;
+constexpr int kMaxCluster = 8;           // CTAs of a cluster sharing one instance's large QR steps
+constexpr int kClusterMinCols = 256;     // expanded bonds from which the QR is split over the cluster
+constexpr size_t kClusterCtlBytes = 256 + 16 * kMaxCluster;
 
 enum DevStatusBits {
   kDevOK = 0,
@@ -59,6 +62,7 @@ struct InstDesc {
   const long long* site_off;  // n+1 offsets (elements of the storage type)
   DevStats* stats;          // device
   void* work;               // device work area for the QR matrices when they exceed shared memory, else null
+  int cluster;              // CTAs that share this instance's large QR steps (thread-block cluster), 1 = none
   double* rec;              // optional: before each iteration, the marked amplitudes and
                             // <s|psi> of the chain, (M+1) complex per iteration
 };
@@ -90,6 +94,7 @@ struct SmemPlan {
   size_t off_chi, off_qb, off_soff, off_terms, off_amps, off_misc, off_qperm, off_qcn, off_tbuf;
   size_t off_tau, off_beta;                          // QR reflector scalars (shared memory)
   size_t off_rprev, off_w;                           // QR matrices (shared memory or the work area)
+  size_t off_refl, off_ctl;                          // work area only: reflectors and the cluster QR's control block
   size_t off_mat, off_u, off_us, off_sig, off_perm;  // SVD sweep (shared memory)
   size_t off_sites;
   size_t total;       // shared-memory bytes
@@ -120,6 +125,14 @@ GMPS_HD SmemPlan make_plan(int n, int M, int xcap, int chicap, int rcap, size_t 
   size_t q = work_global ? 0 : base;
   p.off_rprev = q; q = align_up(q + cb * (size_t)rcap * xcap, 16);
   p.off_w = q;     q = align_up(q + cb * (size_t)(2 * rcap) * xcap, 16);
+  if (work_global) {
+    // a QR split over the CTAs of a cluster exchanges its reflectors and
+    // pivot candidates here
+    p.off_refl = q;  q = align_up(q + cb * (size_t)(2 * rcap) * rcap, 16);
+    p.off_ctl = q;
+    q = align_up(q + kClusterCtlBytes + align_up(sizeof(int) * (size_t)rcap, 16) + align_up(rb * (size_t)rcap, 16) +
+                     cb * (size_t)rcap, 16);
+  }
   p.work_bytes = work_global ? q : 0;
   // SVD-sweep working set (aliases the QR matrices when those are here)
   size_t s = base;
@@ -153,7 +166,7 @@ GMPS_HD long long slot_elems(int l, int n, int rcap) {
 cudaError_t launch_init(const InstDesc* d_desc, int count, int dtype, int threads,
                         cudaStream_t stream);
 cudaError_t launch_iterate(const InstDesc* d_desc, int count, int* d_queue, int dtype,
-                           int threads, size_t smem, int grid, cudaStream_t stream);
+                           int threads, size_t smem, int grid, cudaStream_t stream, int cluster = 1);
 cudaError_t launch_amplitudes(const InstDesc* d_desc, int inst, int dtype,
                               const unsigned long long* d_bits, int nbits,
                               double* d_out /* 2*nbits */, cudaStream_t stream);

@@ -31,8 +31,8 @@ cudaError_t launch_init(const InstDesc* d_desc, int count, int dtype, int thread
 }
 
 cudaError_t launch_iterate(const InstDesc* d_desc, int count, int* d_queue, int dtype, int threads, size_t smem,
-                           int grid, cudaStream_t stream) {
-  return GMPS_DISPATCH(dtype, iterate(d_desc, count, d_queue, threads, smem, grid, stream));
+                           int grid, cudaStream_t stream, int cluster) {
+  return GMPS_DISPATCH(dtype, iterate(d_desc, count, d_queue, threads, smem, grid, stream, cluster));
 }
 
 cudaError_t launch_adjoint(const InstDesc* d_mu, const AdjArgs* d_args, int count, int dtype, int threads,

@@ -66,3 +66,17 @@ def test_flop_model_matches_the_stated_counts():
     assert bench.algorithmic_flops_per_iter(12, 2, 1, "mpo") == pytest.approx(1.8e5, rel=0.02)
     assert bench.algorithmic_flops_per_iter(12, 2, 1, "fused") == pytest.approx(8.6e4, rel=0.05)
     assert bench.algorithmic_flops_per_iter(29, 2, 1, "fused") == pytest.approx(2.27e5, rel=0.01)
+
+
+def test_executed_flop_model_hand_count():
+    """The executed count at n = 2, chi = 1, M = 1 (fused, X = chi + M + 1 = 3,
+    one site step), worked by hand: Householder QR of the 2 x 3 matrix with one
+    reflector, (3 - 1) trailing columns x 2 rows x 20 flops = 80; thin Q from
+    it, 8 x 2 = 16; thin SVD of 1 x 2, 4 (14 * 2 * 1 + 8) = 144; contraction
+    8 * 1 * 2 * 3 = 48 plus the absorption 8 * 1 * 2 * 1 = 16: 304 in all.  At
+    every workload it stays below the nominal full-rank count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.executed_flops_per_iter(2, 1, 1, "fused") == 304
+    for n, chi, M, apply in ((29, 2, 1, "fused"), (40, 33, 32, "fused"), (40, 33, 32, "mpo"), (20, 5, 4, "split")):
+        assert bench.executed_flops_per_iter(n, chi, M, apply) < bench.algorithmic_flops_per_iter(n, chi, M, apply)
