@@ -546,7 +546,7 @@ __device__ __forceinline__ cx<double> ldcg_cx(const cx<double>* p) {
 }
 
 template <class T>
-__device__ int cluster_qr(cx<T>* W, int m, int ncol, cx<T>* Rp, cx<T>* refl, int ldr, const ClusterView<T>& cv,
+__device__ __noinline__ int cluster_qr(cx<T>* W, int m, int ncol, cx<T>* Rp, cx<T>* refl, int ldr, const ClusterView<T>& cv,
                           T floor_rel2, int maxrank, T* cn, int* pstep) {
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
@@ -690,7 +690,7 @@ __device__ int cluster_qr(cx<T>* W, int m, int ncol, cx<T>* Rp, cx<T>* refl, int
 // A cluster CTA other than the first: waits for the first CTA's commands and
 // takes its share of each large QR until told to stop.
 template <class T>
-__device__ void cluster_worker(const InstDesc& d, unsigned char* smem) {
+__device__ __noinline__ void cluster_worker(const InstDesc& d, unsigned char* smem) {
   cg::cluster_group cl = cg::this_cluster();
   const SmemPlan P = make_plan(d.n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), 0, true);
   unsigned char* work = (unsigned char*)d.work;
@@ -1125,11 +1125,48 @@ __device__ __forceinline__ void env_fold(Blk<T, S>& B, int s, int nt, int G, cx<
   E = plus ? cscale(nv, K<CR>::isq2()) : nv;
 }
 
+// The cluster branch of a QR-sweep step (CTA 0): posts the command, factors
+// W (m x xr, work area) with the other CTAs of the cluster, checks the rank
+// against the capacity and stores the thin Q of the exchanged reflectors into
+// the site.  Out of line so that its registers do not weigh on the sweep's
+// hot path.  Returns the rank p >= 1, or 0 after recording a capacity status.
+template <class T, class S>
+__device__ __noinline__ int cluster_qr_step(const InstDesc& d, int n, int m, int xr, T fl, cx<T>* W, cx<T>* Rp,
+                                            T* tau, int* misc, T* qcn, int* qperm, S* dst, unsigned long long key) {
+  const SmemPlan Pw = make_plan(n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), 0, true);
+  unsigned char* work = (unsigned char*)d.work;
+  const ClusterView<T> cv = cluster_view<T>(work, Pw, d.rcap);
+  if (threadIdx.x == 0) {
+    cv.c->op = 1;
+    cv.c->m = m;
+    cv.c->ncol = xr;
+    cv.c->floor_rel2 = (double)(fl * fl);
+    __threadfence();
+  }
+  __syncthreads();
+  cg::this_cluster().sync();  // command posted
+  cx<T>* refl = (cx<T>*)(work + Pw.off_refl);
+  int p = cluster_qr<T>(W, m, xr, Rp, refl, d.rcap, cv, fl * fl, d.rcap, qcn, qperm);
+  if (p < 1) p = 1;
+  if (p > d.rcap) {  // the rank exceeds what R, W and the slots were sized for
+    if (threadIdx.x == 0) set_status<T>(misc, kDevCapacity);
+    __syncthreads();
+    return 0;
+  }
+  for (int j = threadIdx.x; j < p; j += blockDim.x) tau[j] = __ldcg(&cv.tau[j]);
+  __syncthreads();
+  qr_form_q_cluster(refl, m, p, d.rcap, tau);
+  for (int e = threadIdx.x; e < m * p; e += blockDim.x)
+    st_site(dst + e, ldcg_cx(refl + (e / p) * d.rcap + (e % p)), key, e);
+  __syncthreads();
+  return p;
+}
+
 // One contraction followed by the QR sweep and the truncated SVD sweep.  With
 // env_nt > 0 (two or more warps, every bond within 16 lanes, env_nt targets
 // in one warp) warp 1 also computes <target|psi> of the result for the
 // env_nt targets in B.tbits/B.tplus, into B.amps, hidden under the SVD sweep.
-template <class T, class S, class CR>
+template <class T, class S, class CR, bool kCl = false>
 __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* lbnd, cx<T> cpsi,
                            int nt, int env_nt = 0) {
   const InstDesc& d = *B.d;
@@ -1206,35 +1243,12 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       break;
     }
     int p;
-    if constexpr (std::is_same<T, double>::value) {
+    if constexpr (kCl && std::is_same<T, double>::value) {
       if (B.csize > 1 && xr >= kClusterMinCols && d.work != nullptr) {
-        // the whole cluster factors W: post the command, share the columns
-        const SmemPlan Pw = make_plan(n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), 0, true);
-        unsigned char* work = (unsigned char*)d.work;
-        const ClusterView<T> cv = cluster_view<T>(work, Pw, d.rcap);
-        const T fl = rank_floor(B, m, xr);
-        if (threadIdx.x == 0) {
-          cv.c->op = 1;
-          cv.c->m = m;
-          cv.c->ncol = xr;
-          cv.c->floor_rel2 = (double)(fl * fl);
-          __threadfence();
-        }
-        __syncthreads();
-        cg::this_cluster().sync();  // command posted
-        cx<T>* refl = (cx<T>*)(work + Pw.off_refl);
-        p = cluster_qr<T>(B.W, m, xr, B.Rp, refl, d.rcap, cv, fl * fl, d.rcap, B.qcn, B.qperm);
-        if (p < 1) p = 1;
-        if (p > d.rcap) {
-          if (threadIdx.x == 0) set_status<T>(B.misc, kDevCapacity);
-          __syncthreads();
-          return;
-        }
-        for (int j = threadIdx.x; j < p; j += blockDim.x) B.tau[j] = __ldcg(&cv.tau[j]);
-        __syncthreads();
-        qr_form_q_cluster(refl, m, p, d.rcap, B.tau);
-        for (int e = threadIdx.x; e < m * p; e += blockDim.x)
-          st_site(dst + e, ldcg_cx(refl + (e / p) * d.rcap + (e % p)), B.key(l, 0), e);
+        // the whole cluster factors W (out of line: its registers stay off this path)
+        p = cluster_qr_step<T, S>(d, n, m, xr, rank_floor(B, m, xr), B.W, B.Rp, B.tau, B.misc, B.qcn, B.qperm, dst,
+                                  B.key(l, 0));
+        if (p == 0) return;  // capacity status recorded
         if (threadIdx.x == 0) B.qb[l + 1] = p;
         __syncthreads();
         r = p;
@@ -1611,14 +1625,18 @@ __device__ void blk_close(Blk<T, S>& B, const InstDesc& d) {
 }
 
 // ------------------------------------------------------------ the kernel
-template <class T, class S, class CR>
+// kCl: the instance runs on a thread-block cluster (one instance, FP64 QR);
+// the plain instantiation carries none of the cluster code.
+template <class T, class S, class CR, bool kCl>
 __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int count, int* queue) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_idx;
   // a single instance may run on a cluster: the first CTA runs the sweeps,
   // the others take shares of its large QR steps (cluster_worker)
-  const int csize = count == 1 ? (int)cg::this_cluster().num_blocks() : 1;
-  if constexpr (std::is_same<T, double>::value) {
+  constexpr bool kClOn = kCl && std::is_same<T, double>::value;
+  int csize = 1;
+  if constexpr (kClOn) {
+    csize = count == 1 ? (int)cg::this_cluster().num_blocks() : 1;
     if (csize > 1 && cg::this_cluster().block_rank() != 0) {
       cluster_worker<T>(descs[0], smem);
       return;
@@ -1688,7 +1706,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
         // O as an MPO of bond M+1: left boundary (1, e^{i phi}-1, ...)
         for (int a = threadIdx.x; a <= M; a += blockDim.x) B.tcoef[a] = a == 0 ? mk<T>(1, 0) : em1;
         __syncthreads();
-        sweep_pair<T, S, CR>(B, 0, 0, M + 1, B.tcoef, mk<T>(1, 0), 0);
+        sweep_pair<T, S, CR, kCl>(B, 0, 0, M + 1, B.tcoef, mk<T>(1, 0), 0);
         if (B.misc[0] != 0) break;
         // D as an MPO of bond 2: left boundary (-1, 1 - e^{i psi})
         if (threadIdx.x == 0) {
@@ -1696,7 +1714,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
           B.tcoef[1] = opsi;
         }
         __syncthreads();
-        sweep_pair<T, S, CR>(B, 0, 1, 2, B.tcoef, mk<T>(1, 0), 0);
+        sweep_pair<T, S, CR, kCl>(B, 0, 1, 2, B.tcoef, mk<T>(1, 0), 0);
       } else if (d.apply == 1) {
         // O|p> = |p> + (e^{i phi}-1) sum_w p(w)|w>
         for (int t = threadIdx.x; t < M; t += blockDim.x) {
@@ -1756,7 +1774,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
     __syncthreads();
     if (count == 1) break;
   }
-  if constexpr (std::is_same<T, double>::value) {
+  if constexpr (kClOn) {
     if (csize > 1) {  // release the cluster's other CTAs
       const InstDesc& d = descs[0];
       const SmemPlan Pw = make_plan(d.n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), 0, true);
@@ -2212,28 +2230,34 @@ cudaError_t FormLaunch<T, S, CR>::init(const InstDesc* d_desc, int count, cudaSt
 template <class T, class S, class CR>
 cudaError_t FormLaunch<T, S, CR>::iterate(const InstDesc* d_desc, int count, int* d_queue, int threads, size_t smem,
                                           int grid, cudaStream_t stream, int cluster) {
-  auto k = iterate_kernel<T, S, CR>;
+  if constexpr (std::is_same<T, double>::value) {
+    if (cluster > 1 && count == 1) {
+      // one instance on a cluster of `cluster` CTAs (one per SM)
+      auto kc = iterate_kernel<T, S, CR, true>;
+      cudaError_t e = cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cluster, 1, 1);
+      cfg.blockDim = dim3(threads, 1, 1);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, kc, d_desc, count, d_queue);
+      if (e != cudaSuccess) return e;
+      count_launch(1);
+      return cudaGetLastError();
+    }
+  }
+  auto k = iterate_kernel<T, S, CR, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (cluster > 1 && count == 1 && std::is_same<T, double>::value) {
-    // one instance on a cluster of `cluster` CTAs (one per SM)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cluster, 1, 1);
-    cfg.blockDim = dim3(threads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k, d_desc, count, d_queue);
-    if (e != cudaSuccess) return e;
-  } else {
-    k<<<grid, threads, smem, stream>>>(d_desc, count, d_queue);
-  }
+  k<<<grid, threads, smem, stream>>>(d_desc, count, d_queue);
   count_launch(1);
   return cudaGetLastError();
 }
