@@ -880,9 +880,9 @@ __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu,
   const int rp = r + (r & 1);
   const int npairs = rp / 2;
   // A pair is handled by a team of 4 quarters of Q lanes (Q a power of two,
-  // 4Q <= 32): quarter 0 owns row p of Mat, 1 row q, 2 row p of U, 3 row q of
-  // U.  For the Gram entries quarter 0 sums |x_p|^2, 1 |x_q|^2, 2 Re and 3 Im
-  // of conj(x_p) x_q, so every lane issues few T instructions.
+  // 4Q <= 32).  For the Gram entries quarter 0 sums |x_p|^2, 1 |x_q|^2, 2 Re
+  // and 3 Im of conj(x_p) x_q, so every lane issues few T instructions; the
+  // rotation then spreads the columns of both matrices over the whole team.
   const int Q = min(8, pow2_cap32(max(c, r)));
   const int TM = 4 * Q;                 // lanes per team
   const int lane = threadIdx.x & 31;
@@ -890,13 +890,13 @@ __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu,
   const int teams = (blockDim.x >> 5) * (32 / TM);
   const int team = (threadIdx.x >> 5) * (32 / TM) + team_in_warp;
   const int base = (lane / TM) * TM;    // first lane of this team in the warp
-  // every lane of a team takes the same branches (p, q and the Gram entries
-  // are team-uniform), so the team syncs on its own lanes only
-  const unsigned tmask = TM == 32 ? 0xffffffffu : (((1u << TM) - 1u) << base);
+  // with r odd, pair 0 of every round holds the padding row: teams take the
+  // real pairs 1 .. npairs-1 only
+  const int k0 = r & 1;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     int rotated = 0;
     for (int t = 0; t < rp - 1; ++t) {
-      for (int t0 = 0; t0 < npairs; t0 += teams) {
+      for (int t0 = k0; t0 < npairs; t0 += teams) {
         const int k = t0 + team;
         int p = -1, q = -1;
         if (k < npairs) {
@@ -929,31 +929,18 @@ __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu,
         // skip pairs with a row below the noise floor (dropped by the rank rule)
         T cc, sre, sim;
         if (act && jacobi_rotation<T>(a, b, gg, tolf, skip2, cc, sre, sim)) {
-          // row p: c x_p - conj(s) x_q ; row q: c x_q + s x_p
-          const bool rowp = (quarter & 1) == 0;
-          const cx<T> coef = rowp ? mk<T>(-sre, sim) : mk<T>(sre, sim);
-          cx<T>* base_ptr = quarter < 2 ? Mat : U;
-          const int ld = quarter < 2 ? ldm : ldu;
-          const int len = quarter < 2 ? c : r;
-          const int own = rowp ? p : q, oth = rowp ? q : p;
-          // blocks of 4Q columns; the block loop's trip count depends only on
-          // max(c, r) and Q (team-uniform), so every lane of the team reaches
-          // each sync; lanes past their row length only guard their accesses
-          const int span = max(c, r);
-          for (int jb = 0; jb < span; jb += 4 * Q) {
-            cx<T> nv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int j = jb + u * Q + ql;
-              if (j < len) nv[u] = cmac(cscale(base_ptr[own * ld + j], cc), coef, base_ptr[oth * ld + j]);
-            }
-            __syncwarp(tmask);  // both rows read before either is written
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int j = jb + u * Q + ql;
-              if (j < len) base_ptr[own * ld + j] = nv[u];
-            }
-            __syncwarp(tmask);
+          // row p: c x_p - conj(s) x_q ; row q: c x_q + s x_p, for the c
+          // columns of Mat and the r columns of U as one list of column
+          // tasks: lane tl of the team owns tasks tl, tl + TM, ... and updates
+          // both rows at its column (no lane reads what another writes)
+          const cx<T> cq = mk<T>(sre, sim), cp = mk<T>(-sre, sim);
+          for (int e = tl; e < c + r; e += TM) {
+            const bool inm = e < c;
+            cx<T>* rows = inm ? Mat : U;
+            const int ld = inm ? ldm : ldu, j = inm ? e : e - c;
+            const cx<T> xp = rows[p * ld + j], xq = rows[q * ld + j];
+            rows[p * ld + j] = cmac(cscale(xp, cc), cp, xq);
+            rows[q * ld + j] = cmac(cscale(xq, cc), cq, xp);
           }
           rotated = 1;
         }
