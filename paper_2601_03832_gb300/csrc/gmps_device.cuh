@@ -233,6 +233,25 @@ __device__ __forceinline__ Grp make_grp(int G) {
   g.ng = blockDim.x / G;
   return g;
 }
+// Lanes per task for a block-wide sweep of `ntask` column tasks over `rows`
+// rows (Householder updates, norms, Q formation): the power of two G <= 32
+// minimising passes x (rows per lane x 10 + 3 log2 G), the FP64 instructions
+// a warp issues per pass (dot, update and norm per element; three shuffle
+// reductions per task).  Wide groups leave lanes idle on short columns and
+// serialise few tasks; narrow ones take every task in one pass.
+__device__ __forceinline__ int pick_g(int rows, int ntask) {
+  int best = 32, bestc = 0x7fffffff;
+#pragma unroll
+  for (int lg = 0; lg <= 5; ++lg) {
+    const int G = 1 << lg, ng = blockDim.x >> lg;
+    const int cost = ((ntask + ng - 1) / ng) * (((rows + G - 1) >> lg) * 10 + 3 * lg);
+    if (cost < bestc) {
+      bestc = cost;
+      best = G;
+    }
+  }
+  return best;
+}
 
 // Device clock in ns and the SM id, for the per-instance busy-time record.
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -353,19 +372,21 @@ template <class T>
 __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<T>* beta, int* perm, T* cn,
                                  int* ctl, T floor_rel2) {
   const int pmax = min(m, ncol);
-  const int G = pow2_cap32(m);
-  const Grp g = make_grp(G);
+  const int G = pow2_cap32(m);  // lanes on the pivot column
   const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
   // initial column norms
-  for (int t0 = 0; t0 < ncol; t0 += g.ng) {
-    const int c = t0 + g.gid;
-    T s2 = 0;
-    if (c < ncol)
-      for (int i = g.lg; i < m; i += G) s2 += abs2(A[i * lda + c]);
-    s2 = gsum(s2, G);
-    if (c < ncol && g.lg == 0) {
-      cn[c] = s2;
-      perm[c] = c;
+  {
+    const Grp g = make_grp(pick_g(m, ncol));
+    for (int t0 = 0; t0 < ncol; t0 += g.ng) {
+      const int c = t0 + g.gid;
+      T s2 = 0;
+      if (c < ncol)
+        for (int i = g.lg; i < m; i += g.G) s2 += abs2(A[i * lda + c]);
+      s2 = gsum(s2, g.G);
+      if (c < ncol && g.lg == 0) {
+        cn[c] = s2;
+        perm[c] = c;
+      }
     }
   }
   __syncthreads();
@@ -462,25 +483,26 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
     __syncthreads();
     const T tj = tau[j];
     const int ntask = ncol - j - 1;
+    const Grp g = make_grp(pick_g(m - j, ntask));
     for (int t0 = 0; t0 < ntask; t0 += g.ng) {
       const int c = j + 1 + t0 + g.gid;
       const bool act = (t0 + g.gid) < ntask;
       cx<T> w = mk<T>(0, 0);
       if (act)
-        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, A[i * lda + j], A[i * lda + c]);
-      w.re = gsum(w.re, G);
-      w.im = gsum(w.im, G);
+        for (int i = j + g.lg; i < m; i += g.G) w = cmacc(w, A[i * lda + j], A[i * lda + c]);
+      w.re = gsum(w.re, g.G);
+      w.im = gsum(w.im, g.G);
       T s2 = 0;
       if (act) {
         const cx<T> tw = cscale(w, -tj);
-        for (int i = j + g.lg; i < m; i += G) {
+        for (int i = j + g.lg; i < m; i += g.G) {
           cx<T> x = A[i * lda + c];
           if (tj != (T)0) x = cmac(x, A[i * lda + j], tw);
           A[i * lda + c] = x;
           if (i > j) s2 += abs2(x);
         }
       }
-      s2 = gsum(s2, G);
+      s2 = gsum(s2, g.G);
       if (act && g.lg == 0) cn[c] = s2;
     }
     __syncthreads();
@@ -554,17 +576,18 @@ __device__ __noinline__ int cluster_qr(cx<T>* W, int m, int ncol, cx<T>* Rp, cx<
   const int c0 = min(ncol, crank * per), c1 = min(ncol, c0 + per);
   const int nloc = c1 - c0;
   const int pmax = min(m, ncol);
-  const int G = pow2_cap32(m);
-  const Grp g = make_grp(G);
-  for (int t0 = 0; t0 < nloc; t0 += g.ng) {
-    const int lc = t0 + g.gid;
-    T s2 = 0;
-    if (lc < nloc)
-      for (int i = g.lg; i < m; i += G) s2 += abs2(W[i * ncol + c0 + lc]);
-    s2 = gsum(s2, G);
-    if (lc < nloc && g.lg == 0) {
-      cn[lc] = s2;
-      pstep[lc] = -1;
+  {
+    const Grp g = make_grp(pick_g(m, nloc));
+    for (int t0 = 0; t0 < nloc; t0 += g.ng) {
+      const int lc = t0 + g.gid;
+      T s2 = 0;
+      if (lc < nloc)
+        for (int i = g.lg; i < m; i += g.G) s2 += abs2(W[i * ncol + c0 + lc]);
+      s2 = gsum(s2, g.G);
+      if (lc < nloc && g.lg == 0) {
+        cn[lc] = s2;
+        pstep[lc] = -1;
+      }
     }
   }
   __syncthreads();
@@ -643,26 +666,27 @@ __device__ __noinline__ int cluster_qr(cx<T>* W, int m, int ncol, cx<T>* Rp, cx<
     }
     cl.sync();  // reflector j posted
     const T tj = __ldcg(&cv.tau[j]);
+    const Grp g = make_grp(pick_g(m - j, nloc));
     for (int t0 = 0; t0 < nloc; t0 += g.ng) {
       const int lc = t0 + g.gid;
       const bool act = lc < nloc && pstep[lc] < 0;
       const int c = c0 + lc;
       cx<T> w = mk<T>(0, 0);
       if (act)
-        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, ldcg_cx(refl + i * ldr + j), W[i * ncol + c]);
-      w.re = gsum(w.re, G);
-      w.im = gsum(w.im, G);
+        for (int i = j + g.lg; i < m; i += g.G) w = cmacc(w, ldcg_cx(refl + i * ldr + j), W[i * ncol + c]);
+      w.re = gsum(w.re, g.G);
+      w.im = gsum(w.im, g.G);
       T s2 = 0;
       if (act) {
         const cx<T> tw = cscale(w, -tj);
-        for (int i = j + g.lg; i < m; i += G) {
+        for (int i = j + g.lg; i < m; i += g.G) {
           cx<T> x = W[i * ncol + c];
           if (tj != (T)0) x = cmac(x, ldcg_cx(refl + i * ldr + j), tw);
           W[i * ncol + c] = x;
           if (i > j) s2 += abs2(x);
         }
       }
-      s2 = gsum(s2, G);
+      s2 = gsum(s2, g.G);
       if (act && g.lg == 0) cn[lc] = s2;
     }
     __syncthreads();
@@ -710,22 +734,22 @@ __device__ __noinline__ void cluster_worker(const InstDesc& d, unsigned char* sm
 // qr_form_q for reflectors that other CTAs of the cluster wrote (A in global
 // memory): every read of A bypasses L1.
 __device__ inline void qr_form_q_cluster(cx<double>* A, int m, int p, int lda, const double* tau) {
-  const int G = pow2_cap32(m);
-  const Grp g = make_grp(G);
   for (int j = p - 1; j >= 0; --j) {
     const double tj = tau[j];
     const int ntask = p - j - 1;
+    const Grp g = make_grp(pick_g(m - j, ntask));
     for (int t0 = 0; t0 < ntask; t0 += g.ng) {
       const int c = j + 1 + t0 + g.gid;
       const bool act = (t0 + g.gid) < ntask;
       cx<double> w = mk<double>(0, 0);
       if (act)
-        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, ldcg_cx(A + i * lda + j), ldcg_cx(A + i * lda + c));
-      w.re = gsum(w.re, G);
-      w.im = gsum(w.im, G);
+        for (int i = j + g.lg; i < m; i += g.G) w = cmacc(w, ldcg_cx(A + i * lda + j), ldcg_cx(A + i * lda + c));
+      w.re = gsum(w.re, g.G);
+      w.im = gsum(w.im, g.G);
       if (act && tj != 0.0) {
         const cx<double> tw = cscale(w, -tj);
-        for (int i = j + g.lg; i < m; i += G) A[i * lda + c] = cmac(ldcg_cx(A + i * lda + c), ldcg_cx(A + i * lda + j), tw);
+        for (int i = j + g.lg; i < m; i += g.G)
+          A[i * lda + c] = cmac(ldcg_cx(A + i * lda + c), ldcg_cx(A + i * lda + j), tw);
       }
     }
     __syncthreads();
@@ -752,22 +776,21 @@ __device__ inline void qr_form_q_cluster(cx<double>* A, int m, int p, int lda, c
 // Q = H_0 H_1 ... H_{p-1} [I_p; 0], right to left (reflector storage reused).
 template <class T>
 __device__ void qr_form_q(cx<T>* A, int m, int p, int lda, const T* tau) {
-  const int G = pow2_cap32(m);
-  const Grp g = make_grp(G);
   for (int j = p - 1; j >= 0; --j) {
     const T tj = tau[j];
     const int ntask = p - j - 1;
+    const Grp g = make_grp(pick_g(m - j, ntask));
     for (int t0 = 0; t0 < ntask; t0 += g.ng) {
       const int c = j + 1 + t0 + g.gid;
       const bool act = (t0 + g.gid) < ntask;
       cx<T> w = mk<T>(0, 0);
       if (act)
-        for (int i = j + g.lg; i < m; i += G) w = cmacc(w, A[i * lda + j], A[i * lda + c]);
-      w.re = gsum(w.re, G);
-      w.im = gsum(w.im, G);
+        for (int i = j + g.lg; i < m; i += g.G) w = cmacc(w, A[i * lda + j], A[i * lda + c]);
+      w.re = gsum(w.re, g.G);
+      w.im = gsum(w.im, g.G);
       if (act && tj != (T)0) {
         const cx<T> tw = cscale(w, -tj);
-        for (int i = j + g.lg; i < m; i += G) A[i * lda + c] = cmac(A[i * lda + c], A[i * lda + j], tw);
+        for (int i = j + g.lg; i < m; i += g.G) A[i * lda + c] = cmac(A[i * lda + c], A[i * lda + j], tw);
       }
     }
     __syncthreads();
