@@ -74,6 +74,8 @@ struct Plan {
   int cluster;               // CTAs sharing a single instance's large QR steps (1: none)
   size_t smem, site_elems, elem_bytes;
   size_t work_bytes;         // device work area for the QR matrices (0: in shared memory)
+  size_t jc_bytes;           // per-site cache of Jacobi rotations (InstDesc::jcache), 0: none
+  int jbanks;                // its banks (sweep pairs per iteration)
   long long off[kMaxN + 1];  // slot offsets, n+1 used
 };
 
@@ -161,6 +163,11 @@ static gmps_status make_plan_for(const gmps_config* c, bool allow_resident, Plan
       work = true;
     }
     P->work_bytes = work ? sp.work_bytes : 0;
+    // each site's last Jacobi rotations, one bank per sweep pair of an
+    // iteration (the fused and gate-level forms sweep once per operator)
+    const int banks = (c->apply == GMPS_APPLY_FUSED || c->apply == GMPS_APPLY_GATES) ? 1 : 2;
+    P->jbanks = banks;
+    P->jc_bytes = rcap > 2 ? (size_t)banks * c->n * ((size_t)rcap * rcap * 16 + 2 * sizeof(int) * rcap) : 0;
     // a generic MPO with an expanded bond in the hundreds: its QR steps are
     // split over a cluster of CTAs when the instance runs alone (FP64 QR)
     P->cluster = (work && c->apply == GMPS_APPLY_MPO && c->dtype != GMPS_DW && xcap >= kClusterMinCols) ? kMaxCluster : 1;
@@ -186,6 +193,7 @@ struct Slab {  // one chain + its descriptor, statistics and work area, carved f
   DevStats* d_stats = nullptr;
   void* d_sites = nullptr;
   void* d_work = nullptr;
+  void* d_jc = nullptr;  // Jacobi rotation cache (the handle's main chain only)
 };
 
 struct gmps_ctx {
@@ -248,7 +256,7 @@ static char* carve_slab(char* p, const gmps_config* c, const Plan& P, Slab* s) {
 }
 
 static size_t arena_size(const gmps_config* c, const Plan& P) {
-  return slab_bytes(c, P) + a256(sizeof(unsigned long long) * c->M) +
+  return slab_bytes(c, P) + a256(P.jc_bytes) + a256(sizeof(unsigned long long) * c->M) +
          a256(sizeof(unsigned long long) * (c->M + 1)) + a256(sizeof(double) * 2 * (c->M + 1)) +
          a256(sizeof(InstDesc)) + a256(sizeof(unsigned long long));
 }
@@ -263,6 +271,8 @@ static InstDesc base_desc(const gmps_ctx* h, const Slab& s) {
   d.xcap = h->plan.xcap;
   d.rcap = h->plan.rcap;
   d.work = s.d_work;
+  d.jcache = s.d_jc;
+  d.jbanks = h->plan.jbanks;
   d.cluster = h->plan.cluster;
   d.max_sweeps = h->cfg.max_sweeps ? h->cfg.max_sweeps : kDefaultMaxSweeps;
   d.resident = h->plan.resident;
@@ -352,6 +362,8 @@ gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps
     h->own_arena = true;
   }
   char* p = carve_slab(h->arena, &h->cfg, h->plan, &h->main);
+  h->main.d_jc = h->plan.jc_bytes ? p : nullptr;
+  p += a256(h->plan.jc_bytes);
   h->d_marked = (unsigned long long*)p;
   p += a256(sizeof(unsigned long long) * cfg->M);
   h->d_qbits = (unsigned long long*)p;
@@ -895,8 +907,8 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
     }
     const Plan& P = b->plans[i];
     total += a256(sizeof(long long) * (cfgs[i].n + 1)) + a256(sizeof(DevStats)) +
-             a256(P.site_elems * P.elem_bytes) + a256(P.work_bytes) + a256(sizeof(unsigned long long) * cfgs[i].M) +
-             a256(sizeof(double) * 2 * ks[i]);
+             a256(P.site_elems * P.elem_bytes) + a256(P.work_bytes) + a256(P.jc_bytes) +
+             a256(sizeof(unsigned long long) * cfgs[i].M) + a256(sizeof(double) * 2 * ks[i]);
     smem = std::max(smem, P.smem);
     maxx = std::max(maxx, P.xcap);
     cost[i] = (double)ks[i] * cfgs[i].n * std::pow((double)P.xcap, 3.0);
@@ -953,6 +965,9 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
     p += a256(P.site_elems * P.elem_bytes);
     d.work = P.work_bytes ? p : nullptr;
     p += a256(P.work_bytes);
+    d.jcache = P.jc_bytes ? p : nullptr;
+    d.jbanks = P.jbanks;
+    p += a256(P.jc_bytes);
     unsigned long long* mk_ = (unsigned long long*)p;
     p += a256(sizeof(unsigned long long) * c.M);
     d.marked = mk_;
@@ -1168,7 +1183,7 @@ gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int 
                        2 * a256(sizeof(double) * 2 * (size_t)count * K) +
                        a256(sizeof(double) * 2 * (size_t)count * b->every * (M + 1)) +
                        a256(sizeof(double) * count) + a256(sizeof(int)) + site_b * nslab +
-                       a256(b->plan.work_bytes) * 3 * count;
+                       a256(b->plan.work_bytes) * 3 * count + a256(b->plan.jc_bytes) * count;
   cudaError_t e = cudaMalloc(&b->mem, bytes);
   if (e != cudaSuccess) {
     grover_mps_diff_batch_destroy(b);
@@ -1190,6 +1205,7 @@ gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int 
   b->d_p = (double*)p;                        p += a256(sizeof(double) * count);
   b->d_queue = (int*)p;                       p += a256(sizeof(int));
   char* works = p;                            p += a256(b->plan.work_bytes) * 3 * count;
+  char* jcs = p;                              p += a256(b->plan.jc_bytes) * count;
   char* sites = p;
   const RankRule rr = rank_rule_for(cfg->dtype);
   auto desc = [&](int slab) {
@@ -1221,6 +1237,9 @@ gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int 
   b->h_ckpt.resize((size_t)count * (b->nseg + 1));
   for (int i = 0; i < count; ++i) {
     b->h_main[i] = desc(i);
+    // the forward chains cache their Jacobi rotations like a handle's main chain
+    b->h_main[i].jcache = b->plan.jc_bytes ? jcs + a256(b->plan.jc_bytes) * i : nullptr;
+    b->h_main[i].jbanks = b->plan.jbanks;
     b->h_main[i].phi = b->d_ph + (size_t)i * K;
     b->h_main[i].psi = b->d_ph + (size_t)(count + i) * K;
     b->h_work[i] = desc(count + i);

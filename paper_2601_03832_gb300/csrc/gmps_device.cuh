@@ -889,15 +889,21 @@ __device__ __forceinline__ bool jacobi_rotation(T a, T b, cx<T> gg, float tolf, 
 // power-of-two scaling, then normalised in T so that c^2 + |s|^2 = 1 to T's
 // rounding.  A pair is rotated while |g| > tol sqrt(a b); pairs in which a
 // row's squared norm is below `skip2` (noise far under the rank rule's
-// threshold, which the truncation drops) are left alone.  Returns sweeps
-// used, or -1 if max_sweeps was exhausted.
+// threshold, which the truncation drops) are left alone.  U starts as the
+// identity, or (u_given) as the rotation the caller already applied to Mat.
+// The sweeps stop after one that rotated no pair.  (Stopping once every
+// rotation of a sweep is small is not safe: within a cluster of nearly equal
+// singular values a pair with a tiny off-diagonal can still turn by a large
+// angle and move the other pairs' off-diagonals around at first order.)
+// Returns sweeps used, or -1 if max_sweeps was exhausted.
 template <class T>
 __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu, int max_sweeps, float tolf,
-                           T skip2) {
-  for (int i = threadIdx.x; i < r * r; i += blockDim.x) {
-    const int a = i / r, b = i % r;
-    U[a * ldu + b] = mk<T>(a == b ? (T)1 : (T)0, 0);
-  }
+                           T skip2, bool u_given = false) {
+  if (!u_given)
+    for (int i = threadIdx.x; i < r * r; i += blockDim.x) {
+      const int a = i / r, b = i % r;
+      U[a * ldu + b] = mk<T>(a == b ? (T)1 : (T)0, 0);
+    }
   __syncthreads();
   if (r < 2) return 0;
   const int rp = r + (r & 1);
@@ -973,6 +979,35 @@ __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu,
     if (!__syncthreads_or(rotated)) return sweep + 1;
   }
   return -1;
+}
+
+// Mat (r x c, leading dim c) <- U (r x r, leading dim r) Mat in place: the
+// block holds a chunk of columns' results in registers (at most 4 per
+// thread; each output column depends on its own input column only) before
+// writing them back.  Needs r <= 4 blockDim.x.
+template <class T>
+__device__ void rotate_rows(cx<T>* Mat, int r, int c, const cx<T>* U) {
+  const int cw = max(1, (4 * (int)blockDim.x) / r);
+  for (int j0 = 0; j0 < c; j0 += cw) {
+    const int w = min(cw, c - j0), tot = r * w;
+    cx<T> o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = threadIdx.x + u * (int)blockDim.x;
+      o[u] = mk<T>(0, 0);
+      if (e < tot) {
+        const int i = e / w, j = j0 + e % w;
+        for (int a = 0; a < r; ++a) o[u] = cmac(o[u], U[i * r + a], Mat[a * c + j]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = threadIdx.x + u * (int)blockDim.x;
+      if (e < tot) Mat[(e / w) * c + j0 + e % w] = o[u];
+    }
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------ contraction
@@ -1135,6 +1170,22 @@ __device__ __forceinline__ void env_fold(Blk<T, S>& B, int s, int nt, int G, cx<
   E = plus ? cscale(nv, K<CR>::isq2()) : nv;
 }
 
+// Jacobi rotation cache of one instance (InstDesc::jcache): per bank (sweep
+// pair of the iteration) and site, the rotations that site's SVD ended with
+// (rcap^2 complex entries of 16 bytes); then per bank and site two pivot
+// sequences of rcap ints: [0] the one of the QR step that made the site's left
+// bond when the rotations were saved, [1] the one of the current QR sweep.
+// The rows of the site's SVD matrix are that QR's reflectors in pivot order,
+// so the cached rotations only fit while the pivot sequence is unchanged.
+template <class T>
+__device__ __forceinline__ cx<T>* jc_rot(const InstDesc& d, int bank, int l) {
+  return (cx<T>*)((unsigned char*)d.jcache + ((size_t)bank * d.n + l) * d.rcap * d.rcap * 16);
+}
+__device__ __forceinline__ int* jc_piv(const InstDesc& d, int which, int bank, int l) {
+  int* base = (int*)((unsigned char*)d.jcache + (size_t)d.jbanks * d.n * d.rcap * d.rcap * 16);
+  return base + (((size_t)which * d.jbanks + bank) * d.n + l) * d.rcap;
+}
+
 // The cluster branch of a QR-sweep step (CTA 0): posts the command, factors
 // W (m x xr, work area) with the other CTAs of the cluster, checks the rank
 // against the capacity and stores the thin Q of the exchanged reflectors into
@@ -1142,7 +1193,8 @@ __device__ __forceinline__ void env_fold(Blk<T, S>& B, int s, int nt, int G, cx<
 // hot path.  Returns the rank p >= 1, or 0 after recording a capacity status.
 template <class T, class S>
 __device__ __noinline__ int cluster_qr_step(const InstDesc& d, int n, int m, int xr, T fl, cx<T>* W, cx<T>* Rp,
-                                            T* tau, int* misc, T* qcn, int* qperm, S* dst, unsigned long long key) {
+                                            T* tau, int* misc, T* qcn, int* qperm, S* dst, unsigned long long key,
+                                            int* piv_out) {
   const SmemPlan Pw = make_plan(n, d.M, d.xcap, d.chicap, d.rcap, sizeof(T), 0, true);
   unsigned char* work = (unsigned char*)d.work;
   const ClusterView<T> cv = cluster_view<T>(work, Pw, d.rcap);
@@ -1163,7 +1215,10 @@ __device__ __noinline__ int cluster_qr_step(const InstDesc& d, int n, int m, int
     __syncthreads();
     return 0;
   }
-  for (int j = threadIdx.x; j < p; j += blockDim.x) tau[j] = __ldcg(&cv.tau[j]);
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    tau[j] = __ldcg(&cv.tau[j]);
+    if (piv_out != nullptr) piv_out[j] = __ldcg(&cv.piv[j]);
+  }
   __syncthreads();
   qr_form_q_cluster(refl, m, p, d.rcap, tau);
   for (int e = threadIdx.x; e < m * p; e += blockDim.x)
@@ -1176,9 +1231,11 @@ __device__ __noinline__ int cluster_qr_step(const InstDesc& d, int n, int m, int
 // env_nt > 0 (two or more warps, every bond within 16 lanes, env_nt targets
 // in one warp) warp 1 also computes <target|psi> of the result for the
 // env_nt targets in B.tbits/B.tplus, into B.amps, hidden under the SVD sweep.
+// `bank` (0 or 1) names this sweep pair's place in the iteration for the
+// per-site cache of Jacobi rotations (d.jcache).
 template <class T, class S, class CR, bool kCl = false>
 __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* lbnd, cx<T> cpsi,
-                           int nt, int env_nt = 0) {
+                           int nt, int env_nt = 0, int bank = 0) {
   const InstDesc& d = *B.d;
   B.rng = fmix64(B.rng + 0x632be59bd9b4e019ull);  // a fresh rounding key per sweep pair
   const int n = B.n;
@@ -1231,7 +1288,10 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
         } else {
           tiny_q_store<T, S>(a, m, pt, dst, B.key(l, 0));
         }
-        if (threadIdx.x == 0) B.qb[l + 1] = pt;
+        if (threadIdx.x == 0) {
+          B.qb[l + 1] = pt;
+          if (d.jcache != nullptr) jc_piv(d, 1, bank, l + 1)[0] = -1;  // no pivot record: no warm start
+        }
       } else if (pend >= 0) {
         flush_q(pend);
       }
@@ -1257,7 +1317,7 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       if (B.csize > 1 && xr >= kClusterMinCols && d.work != nullptr) {
         // the whole cluster factors W (out of line: its registers stay off this path)
         p = cluster_qr_step<T, S>(d, n, m, xr, rank_floor(B, m, xr), B.W, B.Rp, B.tau, B.misc, B.qcn, B.qperm, dst,
-                                  B.key(l, 0));
+                                  B.key(l, 0), d.jcache != nullptr ? jc_piv(d, 1, bank, l + 1) : nullptr);
         if (p == 0) return;  // capacity status recorded
         if (threadIdx.x == 0) B.qb[l + 1] = p;
         __syncthreads();
@@ -1274,6 +1334,10 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       if (threadIdx.x == 0) set_status<T>(B.misc, kDevCapacity);
       __syncthreads();
       return;
+    }
+    if (d.jcache != nullptr) {
+      int* pv = jc_piv(d, 1, bank, l + 1);
+      for (int c = threadIdx.x; c < p; c += blockDim.x) pv[c] = B.qperm[c];
     }
     // R P^T -> Rp (p x xr, ld xr): column c of the pivoted R is original column perm[c]
     for (int e = threadIdx.x; e < p * xr; e += blockDim.x) {
@@ -1359,7 +1423,29 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
       B.tmisc[8] = B.tmisc[9] * f * f;
     }
     __syncthreads();
-    const int sw = jacobi_rows<T>(B.Mat, rl, c, c, B.U, rl, d.max_sweeps, K<T>::jtolf(), B.tmisc[8]);
+    // warm start: the rotations this site's SVD ended with in the previous
+    // iteration (same sweep pair, same row count) nearly diagonalise the Gram
+    // matrix again, since one Grover iteration turns the state by a small
+    // angle; any unitary start gives the same SVD, so the cache only saves
+    // sweeps
+    cx<T>* jc = (d.jcache != nullptr && rl <= 4 * (int)blockDim.x) ? jc_rot<T>(d, bank, l) : nullptr;
+    int* pv_old = jc != nullptr ? jc_piv(d, 0, bank, l) : nullptr;
+    const int* pv_cur = jc != nullptr ? jc_piv(d, 1, bank, l) : nullptr;
+    int fits = jc != nullptr && d.stats->jrank[bank][l] == rl;
+    if (fits)
+      for (int e = threadIdx.x; e < rl; e += blockDim.x) fits &= (pv_cur[e] >= 0 && pv_cur[e] == pv_old[e]);
+    const bool warm = __syncthreads_and(fits);
+    if (warm) {
+      for (int e = threadIdx.x; e < rl * rl; e += blockDim.x) B.U[e] = jc[e];
+      __syncthreads();
+      rotate_rows<T>(B.Mat, rl, c, B.U);
+    }
+    const int sw = jacobi_rows<T>(B.Mat, rl, c, c, B.U, rl, d.max_sweeps, K<T>::jtolf(), B.tmisc[8], warm);
+    if (jc != nullptr) {
+      for (int e = threadIdx.x; e < rl * rl; e += blockDim.x) jc[e] = B.U[e];
+      for (int e = threadIdx.x; e < rl; e += blockDim.x) pv_old[e] = pv_cur[e];
+      if (threadIdx.x == 0) d.stats->jrank[bank][l] = rl;
+    }
     // row norms -> sigma, ranks -> perm
     {
       const int G = pow2_cap32(c);
@@ -1638,7 +1724,7 @@ __device__ void blk_close(Blk<T, S>& B, const InstDesc& d) {
 // kCl: the instance runs on a thread-block cluster (one instance, FP64 QR);
 // the plain instantiation carries none of the cluster code.
 template <class T, class S, class CR, bool kCl>
-__global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int count, int* queue) {
+__global__ void __launch_bounds__(256, 1) iterate_kernel(const InstDesc* descs, int count, int* queue) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_idx;
   // a single instance may run on a cluster: the first CTA runs the sweeps,
@@ -1724,7 +1810,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
           B.tcoef[1] = opsi;
         }
         __syncthreads();
-        sweep_pair<T, S, CR, kCl>(B, 0, 1, 2, B.tcoef, mk<T>(1, 0), 0);
+        sweep_pair<T, S, CR, kCl>(B, 0, 1, 2, B.tcoef, mk<T>(1, 0), 0, 0, 1);
       } else if (d.apply == 1) {
         // O|p> = |p> + (e^{i phi}-1) sum_w p(w)|w>
         for (int t = threadIdx.x; t < M; t += blockDim.x) {
@@ -1746,7 +1832,7 @@ __global__ void __launch_bounds__(256) iterate_kernel(const InstDesc* descs, int
         chain_targets<T, S, T>(B, 1);
         if (threadIdx.x == 0) B.tcoef[0] = cmul(opsi, B.amps[0]);
         __syncthreads();
-        sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), 1);
+        sweep_pair<T, S, CR>(B, 1, 0, 0, nullptr, mk<T>(-1, 0), 1, 0, 1);
       } else {
         // G|p> = -|p> - (e^{i phi}-1) sum_w p(w)|w> + (1-e^{i psi}) <s|O p> |s>
         for (int t = threadIdx.x; t <= M; t += blockDim.x) {
@@ -1889,7 +1975,7 @@ __device__ void adjoint_two_steps(Blk<T, S>& B, const double* rec, long long k, 
 // costate chain: block b works on descs[b] with the arguments args[b] (a batch
 // of phase vectors of one problem runs as one launch).
 template <class T, class S, class CR>
-__global__ void __launch_bounds__(256) adjoint_kernel(const InstDesc* descs, const AdjArgs* args, long long k_lo,
+__global__ void __launch_bounds__(256, 1) adjoint_kernel(const InstDesc* descs, const AdjArgs* args, long long k_lo,
                                                        long long k_hi, int project) {
   extern __shared__ __align__(16) unsigned char smem[];
   const InstDesc& d = descs[blockIdx.x];
@@ -2008,7 +2094,7 @@ __device__ void apply_1q(Blk<T, S>& B, int l, const double* u) {
 // oracle MPO of the all-ones string, d.marked[0] -- contracted into the sites
 // and recompressed by the QR and truncated SVD sweeps.
 template <class T, class S, class CR>
-__global__ void __launch_bounds__(256) circuit_kernel(const InstDesc* descs, const GateOp* gates, long long count,
+__global__ void __launch_bounds__(256, 1) circuit_kernel(const InstDesc* descs, const GateOp* gates, long long count,
                                                        long long repeat) {
   extern __shared__ __align__(16) unsigned char smem[];
   const InstDesc& d = descs[0];
@@ -2050,7 +2136,11 @@ __global__ void init_kernel(const InstDesc* descs, int count) {
     st(a + 1, mk<double>(h, 0.0));
   }
   DevStats* ds = d.stats;
-  for (int l = threadIdx.x; l <= d.n; l += blockDim.x) ds->chi[l] = 1;
+  for (int l = threadIdx.x; l <= d.n; l += blockDim.x) {
+    ds->chi[l] = 1;
+    ds->jrank[0][l] = 0;
+    ds->jrank[1][l] = 0;
+  }
   if (threadIdx.x == 0) {
     ds->iterations = 0;
     ds->jacobi_sweeps = 0;
@@ -2221,7 +2311,11 @@ __global__ void copy_sites_kernel(const InstDesc* srcs, const InstDesc* dsts) {
   if (blockIdx.x == 0) {
     const int* c0 = src->stats->chi;
     int* c1 = dst->stats->chi;
-    for (int l = threadIdx.x; l <= src->n; l += blockDim.x) c1[l] = c0[l];
+    for (int l = threadIdx.x; l <= src->n; l += blockDim.x) {
+      c1[l] = c0[l];
+      dst->stats->jrank[0][l] = 0;  // the copy starts without cached rotations
+      dst->stats->jrank[1][l] = 0;
+    }
     if (threadIdx.x == 0) {
       dst->stats->status = src->stats->status;
       dst->stats->log_norm = src->stats->log_norm;

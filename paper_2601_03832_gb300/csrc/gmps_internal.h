@@ -35,6 +35,7 @@ struct DevStats {
   int chi[kMaxN + 1];       // bond table after the last sweep pair
   unsigned long long t_begin, t_end;  // device clock (ns) when the last launch began and ended this instance
   int sm;                   // SM that ran it
+  int jrank[2][kMaxN + 1];  // rows of the Jacobi rotations cached per sweep pair and site (0: none)
 };
 
 // Everything one persistent block needs for one instance.  Lives in device
@@ -63,6 +64,9 @@ struct InstDesc {
   DevStats* stats;          // device
   void* work;               // device work area for the QR matrices when they exceed shared memory, else null
   int cluster;              // CTAs that share this instance's large QR steps (thread-block cluster), 1 = none
+  void* jcache;             // device: each site's last Jacobi rotations per sweep pair (the next
+                            // iteration's starting point) and QR pivot sequences; null = none
+  int jbanks;               // sweep pairs per iteration with a cache bank (1 or 2)
   double* rec;              // optional: before each iteration, the marked amplitudes and
                             // <s|psi> of the chain, (M+1) complex per iteration
 };
