@@ -163,11 +163,14 @@ static gmps_status make_plan_for(const gmps_config* c, bool allow_resident, Plan
       work = true;
     }
     P->work_bytes = work ? sp.work_bytes : 0;
-    // each site's last Jacobi rotations, one bank per sweep pair of an
-    // iteration (the fused and gate-level forms sweep once per operator)
+    // the precision forms keep each site's last Jacobi rotations, one bank
+    // per sweep pair of an iteration (the fused and gate-level forms sweep
+    // once per operator); the plain FP64 form always starts from the identity
     const int banks = (c->apply == GMPS_APPLY_FUSED || c->apply == GMPS_APPLY_GATES) ? 1 : 2;
     P->jbanks = banks;
-    P->jc_bytes = rcap > 2 ? (size_t)banks * c->n * ((size_t)rcap * rcap * 16 + 2 * sizeof(int) * rcap) : 0;
+    P->jc_bytes = (rcap > 2 && c->dtype != GMPS_C128)
+                      ? (size_t)banks * c->n * ((size_t)rcap * rcap * 16 + 2 * sizeof(int) * rcap)
+                      : 0;
     // a generic MPO with an expanded bond in the hundreds: its QR steps are
     // split over a cluster of CTAs when the instance runs alone (FP64 QR)
     P->cluster = (work && c->apply == GMPS_APPLY_MPO && c->dtype != GMPS_DW && xcap >= kClusterMinCols) ? kMaxCluster : 1;

@@ -367,10 +367,14 @@ __device__ __forceinline__ int expo_abs(dw x) { return ((__float_as_int(x.h) >> 
 // perm[c] is the original index of the column now at position c; the first
 // `rank` columns hold v_j from row j down, the leading `rank` rows the
 // upper-trapezoidal R of the permuted matrix (diagonal in beta).  cn is
-// scratch for ncol norms; ctl for 4 ints.
+// scratch for ncol norms; ctl for 4 ints.  pref (npref entries, or null): the
+// pivot sequence this step took in the previous iteration; step j takes
+// column pref[j] again while its norm is at least half the largest remaining
+// one, so that the sequence -- and the row basis it gives the next site --
+// stays put between iterations (the stop test still uses the largest norm).
 template <class T>
 __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<T>* beta, int* perm, T* cn,
-                                 int* ctl, T floor_rel2) {
+                                 int* ctl, T floor_rel2, const int* pref = nullptr, int npref = 0) {
   const int pmax = min(m, ncol);
   const int G = pow2_cap32(m);  // lanes on the pivot column
   const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
@@ -395,7 +399,8 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
   for (int j = 0; j < pmax; ++j) {
     if (threadIdx.x == 0) {
       // pivot: largest remaining norm (compared through exact FP32 images)
-      int best = j;
+      const int want = j < npref ? pref[j] : -1;
+      int best = j, keep = perm[j] == want ? j : -1;
       float bv = f32_scaled(cn[j], 0);
       for (int c = j + 1; c < ncol; ++c) {
         const float v = f32_scaled(cn[c], 0);
@@ -403,14 +408,16 @@ __device__ int qr_rank_revealing(cx<T>* A, int m, int ncol, int lda, T* tau, cx<
           bv = v;
           best = c;
         }
+        if (perm[c] == want) keep = c;
       }
-      ctl[0] = best;
       if (j == 0) {
         ctl[1] = 0;
         // floor relative to the largest column norm of the input
         *(T*)(ctl + 2) = cn[best] * floor_rel2;
       }
       ctl[1] = (j > 0 && !(cn[best] > *(T*)(ctl + 2))) ? 1 : 0;
+      if (keep >= 0 && f32_scaled(cn[keep], 0) >= 0.5f * bv) best = keep;
+      ctl[0] = best;
       if (ctl[1] == 0 && best != j) {
         const T tc = cn[j];
         cn[j] = cn[best];
@@ -1327,7 +1334,12 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     }
     {
       const T fl = rank_floor(B, m, xr);
-      p = qr_rank_revealing<T>(B.W, m, xr, xr, B.tau, B.beta, B.qperm, B.qcn, B.misc + 8, fl * fl);
+      // the pivot sequence saved with site l+1's rotations, unless that came
+      // from a register-resident QR step (no record)
+      const int* pref = d.jcache != nullptr ? jc_piv(d, 0, bank, l + 1) : nullptr;
+      const int npref = (pref != nullptr && d.stats->jrank[bank][l + 1] > 0 && pref[0] >= 0)
+                            ? d.stats->jrank[bank][l + 1] : 0;
+      p = qr_rank_revealing<T>(B.W, m, xr, xr, B.tau, B.beta, B.qperm, B.qcn, B.misc + 8, fl * fl, pref, npref);
     }
     if (p < 1) p = 1;
     if (p > d.rcap) {  // the rank exceeds what R, W and the slots were sized for
