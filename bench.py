@@ -33,7 +33,7 @@ SAMPLE_SEED = 2
 # k): DRAM bytes (read + write) per launch, and the FP64 pipe busy share of the
 # SM running the instance (sm__pipe_fp64_cycles_active, summed over its four
 # sub-partitions).  None until a capture of the current kernel is recorded.
-CAPTURE = {"traffic_bytes": 227584, "fp64_pipe_share": 4 * 0.14789}
+CAPTURE = {"traffic_bytes": 206336, "fp64_pipe_share": 4 * 0.15113}
 
 
 def flops_per_iter_parts(n: int, chi: int, M: int, apply: str):
@@ -311,21 +311,25 @@ def extra_workloads(B, inputs, sptr, peaks):
                     "total_instance_s": sum(busy.values())},
         "roofline": rl}
     bt.close()
-    # multi-marked n = 40, M = 32, chi_max = 128, tol = 1e-12, full k = 1000
+    # multi-marked n = 40, M = 32, chi_max = 128, tol = 1e-12, full k = 1000,
+    # in the plain FP64 form and in the two precision forms
     mi = inputs.config_multi_marked(k=1000)
-    g = B.GroverMPS(mi.n, mi.marked, dtype="c128", apply=APPLY, chi_max=mi.chi_max, tol=mi.tol, stream=sptr)
-    g.iterate(1)                                                   # warm-up iteration
-    g.reset()
-    sec, _ = timed(lambda: g.iterate(mi.k))
-    p = g.prob_marked()
     Pm = reduced.closed_form(mi.n, mi.M, mi.k)[0]
-    chi = g.stats()["max_bond"]
-    out["n40_M32_c128"] = {"iterations_per_s": mi.k / sec, "k": mi.k, "seconds": sec, "P_marked": p,
-                           "P_closed_form": Pm, "P_rel_err": (p - Pm) / Pm, "max_bond": chi,
-                           "roofline": roofline_alu(mi.k * executed_flops_per_iter(mi.n, chi, mi.M, APPLY),
-                                                    sec, fp64, "FP64 FMA", 1, sms,
-                                                    mi.k * algorithmic_flops_per_iter(mi.n, chi, mi.M, APPLY))}
-    g.close()
+    for dt, peak, pname in (("c128", fp64, "FP64 FMA"), ("c64", fp64, "FP64 FMA"), ("dw", fp32, "FP32 FMA")):
+        g = B.GroverMPS(mi.n, mi.marked, dtype=dt, apply=APPLY, chi_max=mi.chi_max, tol=mi.tol, stream=sptr)
+        g.iterate(1)                                                   # warm-up iteration
+        g.reset()
+        sec, _ = timed(lambda: g.iterate(mi.k))
+        p = g.prob_marked()
+        st_ = g.stats()
+        chi = st_["max_bond"]
+        out["n40_M32_" + dt] = {
+            "iterations_per_s": mi.k / sec, "k": mi.k, "seconds": sec, "P_marked": p, "P_closed_form": Pm,
+            "P_rel_err": (p - Pm) / Pm, "max_bond": chi,
+            "jacobi_sweeps_per_svd": st_["jacobi_sweeps"] / max(1, st_["svd_count"]),
+            "roofline": roofline_alu(mi.k * executed_flops_per_iter(mi.n, chi, mi.M, APPLY), sec, peak, pname, 1, sms,
+                                     mi.k * algorithmic_flops_per_iter(mi.n, chi, mi.M, APPLY))}
+        g.close()
     # the same instance with the oracle as a generic MPO of bond M + 1 = 33
     # (expanded bond 33 x 35 = 1155; QR matrices in the device work area),
     # a k = 5 slice
