@@ -850,16 +850,20 @@ __device__ __forceinline__ bool nn_eq<double>(double a, double b) {
 // (normalised through rho = c^2 + |s|^2, or for small angles through c).
 // The angle is kept to IEEE FP32 accuracy (not MUFU estimates): a sloppier
 // angle costs extra rotations, whose rounding lifts the noise rows of
-// rank-deficient matrices toward the rank rule's threshold.
+// rank-deficient matrices toward the rank rule's threshold.  `small` (when
+// given) is set when the pair rotates with |g| <= 2^-32 sqrt(a b).
 template <class T>
-__device__ __forceinline__ bool jacobi_rotation(T a, T b, cx<T> gg, float tolf, T skip2, T& cc, T& sre, T& sim) {
+__device__ __forceinline__ bool jacobi_rotation(T a, T b, cx<T> gg, float tolf, T skip2, T& cc, T& sre, T& sim,
+                                                bool* small = nullptr) {
   if (!(nn_gt(a, skip2) && nn_gt(b, skip2))) return false;
   const int sh = expo_of(nn_gt(a, b) ? a : b);
   const float af = f32_scaled(a, sh), bf = f32_scaled(b, sh);
   const float dab = f32_scaled(b - a, sh);  // difference taken in T
   const float gr = f32_scaled(gg.re, sh), gi = f32_scaled(gg.im, sh);
   const float gabs = sqrtf(fmaf(gr, gr, gi * gi));
-  if (!(gabs > tolf * sqrtf(af) * sqrtf(bf) && gabs > 0.f)) return false;
+  const float sab = sqrtf(af) * sqrtf(bf);
+  if (!(gabs > tolf * sab && gabs > 0.f)) return false;
+  if (small != nullptr) *small = gabs <= 2.3283064e-10f * sab;
   const float zeta = dab / (2.f * gabs);
   // small-root formula; for |zeta| > 2^60 (zeta^2 would overflow) t = 1/(2 zeta)
   const float tt = fabsf(zeta) > 1.1529215e18f ? 0.5f / zeta

@@ -276,6 +276,12 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
   // without rotating)
   int sw = 0;
   T own2 = 0;
+  // a single pair (rl == 2) whose rotation had |g| <= 2^-32 sqrt(a b) is
+  // done: the FP32 angle leaves at most ~1.6 * 2^-22 of that off-diagonal and
+  // FP64 rounding ~2^-53, both far below the rotation threshold, so the sweep
+  // that would confirm it rotates nothing and is skipped (the row norms are
+  // then summed afresh, as that sweep's Gram diagonal would give them)
+  bool done_early = false;
   if (rl >= 2) {
     sw = -1;
     const int nround = rl == 2 ? 1 : 3;
@@ -311,15 +317,17 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
           own2 = isP ? a : b;
         }
         T cc, sre, sim;
-        const bool rot = p < rl && q < rl && jacobi_rotation<T>(a, b, gg, K<T>::jtolf(), skip2, cc, sre, sim);
+        bool small = false;
+        const bool rot = p < rl && q < rl && jacobi_rotation<T>(a, b, gg, K<T>::jtolf(), skip2, cc, sre, sim, &small);
         if (rot) {
           // row p: c x_p - conj(s) x_q ; row q: c x_q + s x_p
           const cx<T> coef = isP ? mk<T>(-sre, sim) : mk<T>(sre, sim);
           x = cmac(cscale(x, cc), coef, y);
         }
         rotated = rotated || rot;
+        if (rl == 2 && __any_sync(0xffffffffu, rot && small)) done_early = true;
       }
-      if (!__any_sync(0xffffffffu, rotated)) {
+      if (!__any_sync(0xffffffffu, rotated) || done_early) {
         sw = sweep + 1;
         break;
       }
@@ -327,7 +335,7 @@ __device__ void tiny_svd_step(Blk<T, S>& B, int l, int rl, int rr, int kr) {
   }
   // sigma_p^2 (rows are orthogonal): the last sweep's Gram diagonal when it
   // rotated nothing, else summed afresh; ranks, rank rule
-  const T sp = sw > 0 ? (row ? own2 : (T)0) : sum8(inM ? abs2(x) : (T)0);
+  const T sp = (sw > 0 && !done_early) ? (row ? own2 : (T)0) : sum8(inM ? abs2(x) : (T)0);
   const T s0 = shidx(sp, 0), s1 = shidx(sp, 8), s2 = shidx(sp, 16), s3 = shidx(sp, 24);
   int rk[4];
 #pragma unroll
