@@ -5,8 +5,11 @@ how many lane groups share each factorisation and how many blocks fit on an
 SM (shared memory and 2048 threads per SM).  `tune_batch` times the actual
 batch on a short slice of its iterations (k_i capped) for each candidate
 block size through the C ABI and keeps the fastest; results are cached in a
-JSON file keyed by (dtype, contraction mode, largest expanded bond, batch
-size), so later runs reuse them.
+JSON file keyed by (GPU name and SM count, library build, dtype, contraction
+mode, largest expanded bond, batch size), so later runs on the same device
+and build reuse them.  Within a block, the lanes per task of each Householder
+step are chosen on the device by a cost model of the step's rows and columns
+(`pick_g` in the kernels), not here.
 """
 from __future__ import annotations
 
@@ -22,13 +25,26 @@ CACHE = os.environ.get("GMPS_TUNE_CACHE",
 CANDIDATES = (64, 128, 256)
 
 
+def _device_tag():
+    """The GPU (name and SM count) and the library build the timings belong to."""
+    import torch
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    try:
+        st = os.stat(binding.LIB_PATH)
+        build = f"{st.st_size}-{int(st.st_mtime)}"
+    except (OSError, AttributeError):
+        build = "unknown"
+    return f"{props.name}|sm{props.multi_processor_count}|{build}"
+
+
 def _key(insts, dtype, apply):
     xcap = 0
     for i in insts:
         chi = min(i.chi_max, i.M + 3)
         x = {"fused": chi + i.M + 1, "split": chi + i.M}.get(apply, (i.M + 1) * chi)
         xcap = max(xcap, x)
-    return f"{dtype}|{apply}|x{xcap}|b{len(insts)}"
+    return f"{_device_tag()}|{dtype}|{apply}|x{xcap}|b{len(insts)}"
 
 
 def _load():

@@ -260,3 +260,21 @@ def test_paper_experiments_small_n(B):
             s = int(s)
             assert 0 <= cnt <= s
             assert abs(cnt - s * Pc) <= 6 * math.sqrt(s * Pc * (1 - Pc)) + 1
+
+
+def test_autotune_picks_a_candidate_and_caches_per_device(B, tmp_path, monkeypatch):
+    """The batch autotuner times every candidate block size on a slice of the
+    batch, returns the fastest, and caches it under a key that names the GPU,
+    its SM count and the library build; a second call is served from the cache."""
+    import torch
+    from paper_2601_03832_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    insts = inputs.config_batched(count=8, seed=9, n_range=(8, 12), m_range=(1, 3), kcap=20, chi_max=8)
+    best, rec = autotune.tune_batch(insts, dtype="c64", apply="fused", kslice=4)
+    assert best in autotune.CANDIDATES
+    assert set(rec["seconds"]) == {str(t) for t in autotune.CANDIDATES}
+    key = autotune._key(insts, "c64", "fused")
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    assert key.startswith(f"{props.name}|sm{props.multi_processor_count}|")
+    best2, rec2 = autotune.tune_batch(insts, dtype="c64", apply="fused", kslice=4)
+    assert best2 == best and rec2 == rec
