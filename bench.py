@@ -33,7 +33,7 @@ SAMPLE_SEED = 2
 # k): DRAM bytes (read + write) per launch, and the FP64 pipe busy share of the
 # SM running the instance (sm__pipe_fp64_cycles_active, summed over its four
 # sub-partitions).  None until a capture of the current kernel is recorded.
-CAPTURE = {"traffic_bytes": 206336, "fp64_pipe_share": 4 * 0.15113}
+CAPTURE = {"traffic_bytes": 209152, "fp64_pipe_share": 4 * 0.15512}
 
 
 def flops_per_iter_parts(n: int, chi: int, M: int, apply: str):
