@@ -223,6 +223,71 @@ print(json.dumps({{"iters": done, "seconds": dt}}))
                       f"({APPLY} contraction, NumPy FP64, OMP_NUM_THREADS=1), {res['seconds']:.1f} s"}
 
 
+def _oracle_batched_slice(task):
+    """One instance of the batched workload on the oracle (process-pool task)."""
+    n, marked, k, chi_max = task
+    from oracle import mps
+    t0 = time.perf_counter()
+    mps.grover_iterate(mps.plus_state(n), marked, k, chi_max, 0.0, mode=APPLY)
+    return k, time.perf_counter() - t0
+
+
+def _oracle_adjoint_vector(task):
+    """Forward and adjoint of one phase vector on the oracle (process-pool task)."""
+    n, marked, phi, psi = task
+    from oracle import statevector
+    t0 = time.perf_counter()
+    statevector.adjoint(n, marked, phi, psi)
+    return time.perf_counter() - t0
+
+
+def _oracle_pool(fn, tasks, workers):
+    """Run oracle tasks on `workers` spawned processes with one BLAS thread
+    each; returns (results, wall seconds)."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+    keep = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in keep:
+        os.environ[v] = "1"
+    try:
+        t0 = time.perf_counter()
+        with ProcessPoolExecutor(max_workers=workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+            res = list(ex.map(fn, tasks))
+        wall = time.perf_counter() - t0
+    finally:
+        for v, x in keep.items():
+            if x is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = x
+    return res, wall
+
+
+def cpu_baseline_batched(insts, kslice: int = 10, count: int = 64):
+    """The oracle on a bounded sample of the batched workload: the first
+    `count` instances, `kslice` iterations each, spread over all host cores."""
+    cores = os.cpu_count() or 1
+    tasks = [(x.n, list(x.marked), min(x.k, kslice), x.chi_max) for x in insts[:count]]
+    res, wall = _oracle_pool(_oracle_batched_slice, tasks, cores)
+    its = sum(r[0] for r in res)
+    return {"value": its / wall, "unit": "iterations/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {len(tasks)} of the 512 instances, min(k_i, {kslice}) iterations each "
+                      f"({its} in all), NumPy FP64 MPS, {cores} spawned processes with one BLAS thread, "
+                      f"{wall:.1f} s wall including process start-up"}
+
+
+def cpu_baseline_differentiable(di, phi, psi, vectors: int = 4):
+    """The oracle's forward + adjoint (dense FP64 statevector, n = 20) on a
+    bounded sample of the phase vectors, one process per vector."""
+    workers = min(vectors, os.cpu_count() or 1)
+    tasks = [(di.n, list(di.marked), phi[b], psi[b]) for b in range(vectors)]
+    res, wall = _oracle_pool(_oracle_adjoint_vector, tasks, workers)
+    return {"value": 1000.0 * wall / vectors, "unit": "ms per vector (forward + backward)", "cores": workers,
+            "kind": "oracle",
+            "sample": f"{vectors} of the 64 phase vectors, dense FP64 statevector forward and adjoint, "
+                      f"{workers} spawned processes, {wall:.1f} s wall (per-vector CPU {max(res):.1f} s)"}
+
+
 def extra_workloads(B, inputs, sptr, peaks):
     """The other forms and workloads, each measured once outside the headline's
     timed region (CUDA events on the handle's stream), each with its error
@@ -311,6 +376,7 @@ def extra_workloads(B, inputs, sptr, peaks):
                     "total_instance_s": sum(busy.values())},
         "roofline": rl}
     bt.close()
+    out["batched_512_c64"]["cpu_baseline"] = cpu_baseline_batched(insts)
     # multi-marked n = 40, M = 32, chi_max = 128, tol = 1e-12, full k = 1000,
     # in the plain FP64 form and in the two precision forms
     mi = inputs.config_multi_marked(k=1000)
@@ -371,7 +437,8 @@ def extra_workloads(B, inputs, sptr, peaks):
     out["differentiable_n20_M4_K64"] = {"fwd_bwd_ms_per_vector": 1000 * sec / len(phi), "vectors": len(phi),
                                         "wall_s": sec, "max_err_vs_reduced_model": worst,
                                         "roofline": roofline_alu(dflops, sec, fp64, "FP64 FMA",
-                                                                 min(len(phi), sms), sms, dnom)}
+                                                                 min(len(phi), sms), sms, dnom),
+                                        "cpu_baseline": cpu_baseline_differentiable(di, phi, psi)}
     return out
 
 
