@@ -923,7 +923,10 @@ __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu,
   // 4Q <= 32).  For the Gram entries quarter 0 sums |x_p|^2, 1 |x_q|^2, 2 Re
   // and 3 Im of conj(x_p) x_q, so every lane issues few T instructions; the
   // rotation then spreads the columns of both matrices over the whole team.
-  const int Q = min(8, pow2_cap32(max(c, r)));
+  // Q: at most 8, and small enough that every real pair of a round has its
+  // own team (one pass per round) while Q >= 2
+  int Q = min(8, pow2_cap32(max(c, r)));
+  while (Q > 2 && (int)(blockDim.x >> 5) * (32 / (4 * Q)) < r / 2) Q >>= 1;
   const int TM = 4 * Q;                 // lanes per team
   const int lane = threadIdx.x & 31;
   const int team_in_warp = lane / TM, tl = lane % TM, quarter = tl / Q, ql = tl % Q;
