@@ -217,6 +217,13 @@ gmps_status grover_mps_destroy(gmps_handle h);
 /* Thread-local message describing the last failing call on this thread. */
 const char* grover_mps_last_error(void);
 
+/* Fault injection for tests: the next `count` device allocations of this
+ * library (handles, batches, statevectors, their buffers) fail as if the
+ * device were out of memory, so that the caller sees GMPS_ERR_OOM and
+ * nothing half-built is left behind.  0 clears it.  count < 0:
+ * GMPS_ERR_ARG.  Process-wide; no CUDA call. */
+gmps_status grover_mps_debug_fail_allocations(int count);
+
 /* ------------------------------------------------------------------ */
 /* Batched: many independent instances in one persistent launch.        */
 /* ------------------------------------------------------------------ */

@@ -33,7 +33,7 @@ EXPORTS = [
     "grover_mps_batch_destroy",
     "grover_mps_launch_count", "grover_mps_run_noalloc", "grover_mps_diff_batch_create",
     "grover_mps_diff_batch_run", "grover_mps_diff_batch_destroy", "grover_mps_apply_circuit",
-    "grover_mps_grover_gates",
+    "grover_mps_grover_gates", "grover_mps_debug_fail_allocations",
 ]
 # every symbol include/grover_sv.h declares
 SV_EXPORTS = [
@@ -120,6 +120,7 @@ def load():
         "grover_mps_diff_batch_create": [P(gmps_config), i32, i32, vp, P(vp)],
         "grover_mps_diff_batch_run": [vp, P(f64), P(f64), P(f64), P(f64), P(f64)],
         "grover_mps_diff_batch_destroy": [vp],
+        "grover_mps_debug_fail_allocations": [i32],
         "grover_sv_bytes": [i32, i32, P(C.c_size_t)],
         "grover_sv_create": [i32, P(u64), i32, i32, vp, P(vp)],
         "grover_sv_reset": [vp],
@@ -152,6 +153,11 @@ def _dptr(a):
 
 def launch_count() -> int:
     return int(load().grover_mps_launch_count())
+
+
+def debug_fail_allocations(count: int):
+    """Make the library's next `count` device allocations fail (tests)."""
+    _check(load().grover_mps_debug_fail_allocations(count))
 
 
 def make_config(n, marked, dtype="c128", apply="mpo", chi_max=4, tol=0.0, max_sweeps=0, threads=0,

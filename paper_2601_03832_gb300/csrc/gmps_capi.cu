@@ -3,7 +3,10 @@
 // propagation.  All compute runs in gmps_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -215,6 +218,7 @@ struct gmps_ctx {
   double* d_qout = nullptr;               // 2(M+1)
   InstDesc* d_cdesc = nullptr;            // gate-level circuits: the chain with the all-ones string
   unsigned long long* d_ones = nullptr;
+  unsigned char* d_canary = nullptr;  // the arena's closing canary (last kCanaryBytes)
   GateOp* d_gates = nullptr;
   size_t gate_cap = 0;
   double* d_phase = nullptr;
@@ -239,6 +243,39 @@ struct gmps_ctx {
   bool all_phases_explicit = true;
 };
 
+// forced device-allocation failures left (grover_mps_debug_fail_allocations)
+static std::atomic<int> g_fail_allocs{0};
+
+cudaError_t gmps::dev_malloc(void** p, size_t bytes) {
+  int c = g_fail_allocs.load();
+  while (c > 0 && !g_fail_allocs.compare_exchange_weak(c, c - 1)) {
+  }
+  if (c > 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+// A canary of 32 distinct 64-bit words closes every handle's arena; it is
+// written at creation and compared after every call that synchronises, so a
+// kernel writing past the instance's slabs shows as GMPS_ERR_STATE.
+static constexpr size_t kCanaryBytes = 256;
+static const unsigned long long* canary_words() {
+  static unsigned long long w[kCanaryBytes / 8];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (size_t i = 0; i < kCanaryBytes / 8; ++i) w[i] = 0x9e3779b97f4a7c15ull * (i + 1) ^ 0xc0ffee0ddba11ull;
+  });
+  return w;
+}
+
+// NVTX range over one C-ABI call (visible to profilers; no cost otherwise)
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+};
+
 static size_t slab_bytes(const gmps_config* c, const Plan& P) {
   return a256(sizeof(InstDesc)) + a256(sizeof(long long) * (c->n + 1)) + a256(sizeof(DevStats)) +
          a256(P.site_elems * P.elem_bytes) + a256(P.work_bytes);
@@ -259,7 +296,7 @@ static char* carve_slab(char* p, const gmps_config* c, const Plan& P, Slab* s) {
 }
 
 static size_t arena_size(const gmps_config* c, const Plan& P) {
-  return slab_bytes(c, P) + a256(P.jc_bytes) + a256(sizeof(unsigned long long) * c->M) +
+  return slab_bytes(c, P) + a256(P.jc_bytes) + kCanaryBytes + a256(sizeof(unsigned long long) * c->M) +
          a256(sizeof(unsigned long long) * (c->M + 1)) + a256(sizeof(double) * 2 * (c->M + 1)) +
          a256(sizeof(InstDesc)) + a256(sizeof(unsigned long long));
 }
@@ -301,8 +338,14 @@ static gmps_status upload_slab(gmps_ctx* h, const Slab& s) {
 
 static gmps_status check_device(gmps_ctx* h) {
   DevStats ds;
+  unsigned long long can[kCanaryBytes / 8];
   CUDA_TRY(cudaMemcpyAsync(&ds, h->main.d_stats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(can, h->d_canary, kCanaryBytes, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (memcmp(can, canary_words(), kCanaryBytes) != 0) {
+    h->error = GMPS_ERR_STATE;
+    return fail(GMPS_ERR_STATE, "arena canary overwritten: a write went past the instance's arena");
+  }
   if (ds.status != 0) {
     h->error = ds.status;
     const char* what = ds.status == kDevNoConv   ? "Jacobi SVD did not converge"
@@ -318,6 +361,12 @@ extern "C" {
 
 const char* grover_mps_last_error(void) { return g_err.c_str(); }
 
+gmps_status grover_mps_debug_fail_allocations(int count) {
+  if (count < 0) return fail(GMPS_ERR_ARG, "count must be >= 0");
+  g_fail_allocs.store(count);
+  return GMPS_OK;
+}
+
 int64_t grover_mps_launch_count(void) { return gmps::launches_so_far(); }
 
 gmps_status grover_mps_arena_bytes(const gmps_config* cfg, size_t* bytes) {
@@ -331,6 +380,7 @@ gmps_status grover_mps_arena_bytes(const gmps_config* cfg, size_t* bytes) {
 }
 
 gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps_handle* out) {
+  CallRange range_("grover_mps_create_ex");
   if (!out) return fail(GMPS_ERR_ARG, "out is NULL");
   *out = nullptr;
   gmps_status s = validate(cfg);
@@ -357,7 +407,7 @@ gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps
     }
     h->arena = (char*)cfg->arena;
   } else {
-    cudaError_t e = cudaMalloc(&h->arena, h->arena_bytes);
+    cudaError_t e = dev_malloc((void**)&h->arena, h->arena_bytes);
     if (e != cudaSuccess) {
       delete h;
       return fail(GMPS_ERR_OOM, std::string("arena allocation: ") + cudaGetErrorString(e));
@@ -376,8 +426,11 @@ gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps
   h->d_cdesc = (InstDesc*)p;
   p += a256(sizeof(InstDesc));
   h->d_ones = (unsigned long long*)p;
-  cudaError_t e = cudaMemcpyAsync(h->d_marked, h->marked.data(), sizeof(uint64_t) * cfg->M,
-                                  cudaMemcpyHostToDevice, h->stream);
+  h->d_canary = (unsigned char*)h->arena + h->arena_bytes - kCanaryBytes;
+  cudaError_t e = cudaMemcpyAsync(h->d_canary, canary_words(), kCanaryBytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_marked, h->marked.data(), sizeof(uint64_t) * cfg->M, cudaMemcpyHostToDevice,
+                        h->stream);
   if (e != cudaSuccess) {
     grover_mps_destroy(h);
     return cuda_fail(e, "upload marked");
@@ -398,7 +451,7 @@ gmps_status grover_mps_create_ex(const gmps_config* cfg, void* cuda_stream, gmps
     const size_t sb = slab_bytes(&h->cfg, h->plan);
     const size_t bytes = sb * (nck + 2) + a256(sizeof(double) * 2 * (cfg->M + 1) * h->every) +
                          2 * a256(sizeof(double) * 2 * h->max_iters) + a256(sizeof(AdjArgs) * 2);
-    cudaError_t e2 = cudaMalloc(&h->diff_mem, bytes);
+    cudaError_t e2 = dev_malloc((void**)&h->diff_mem, bytes);
     if (e2 != cudaSuccess) {
       grover_mps_destroy(h);
       return fail(GMPS_ERR_OOM, "checkpoint storage");
@@ -462,7 +515,7 @@ static gmps_status ensure_phase(gmps_ctx* h, size_t need) {
   if (h->d_phase) cudaFree(h->d_phase);
   h->d_phase = nullptr;
   size_t cap = std::max<size_t>(need, 1024);
-  cudaError_t e = cudaMalloc(&h->d_phase, sizeof(double) * 2 * cap);
+  cudaError_t e = dev_malloc((void**)&h->d_phase, sizeof(double) * 2 * cap);
   if (e != cudaSuccess) return fail(GMPS_ERR_OOM, "phase buffer");
   h->phase_cap = cap;
   return GMPS_OK;
@@ -483,6 +536,7 @@ static gmps_status enqueue_iterate(gmps_ctx* h, int64_t k, const double* dphi, c
 }
 
 gmps_status grover_mps_iterate_device(gmps_handle h, int64_t k, const double* dev_phi, const double* dev_psi) {
+  CallRange range_("grover_mps_iterate_device");
   if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
   if (h->cfg.apply == GMPS_APPLY_GATES)
     return fail(GMPS_ERR_UNSUPPORTED, "a gate-level handle takes circuits (grover_mps_apply_circuit)");
@@ -499,6 +553,7 @@ gmps_status grover_mps_iterate_device(gmps_handle h, int64_t k, const double* de
 }
 
 gmps_status grover_mps_iterate(gmps_handle h, int64_t k, const double* host_phi, const double* host_psi) {
+  CallRange range_("grover_mps_iterate");
   if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
   if (h->cfg.apply == GMPS_APPLY_GATES)
     return fail(GMPS_ERR_UNSUPPORTED, "a gate-level handle takes circuits (grover_mps_apply_circuit)");
@@ -598,6 +653,7 @@ gmps_status grover_mps_sample_device(gmps_handle h, int64_t shots, uint64_t seed
 }
 
 gmps_status grover_mps_sample(gmps_handle h, int64_t shots, uint64_t seed, uint64_t* out_bits) {
+  CallRange range_("grover_mps_sample");
   if (!h || (!out_bits && shots > 0)) return fail(GMPS_ERR_ARG, "NULL argument");
   if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
   if (shots < 0) return fail(GMPS_ERR_ARG, "shots must be >= 0");
@@ -605,7 +661,7 @@ gmps_status grover_mps_sample(gmps_handle h, int64_t shots, uint64_t seed, uint6
   if ((size_t)shots > h->sample_cap) {
     if (h->d_sample) cudaFree(h->d_sample);
     h->d_sample = nullptr;
-    cudaError_t e = cudaMalloc(&h->d_sample, sizeof(uint64_t) * shots);
+    cudaError_t e = dev_malloc((void**)&h->d_sample, sizeof(uint64_t) * shots);
     if (e != cudaSuccess) return fail(GMPS_ERR_OOM, "sample buffer");
     h->sample_cap = shots;
   }
@@ -693,6 +749,7 @@ static gmps_status check_slab(gmps_ctx* h, const Slab& sl, const char* what) {
 }
 
 gmps_status grover_mps_backward(gmps_handle h, double dL_dP, double* grad_phi, double* grad_psi) {
+  CallRange range_("grover_mps_backward");
   if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
   if (!h->cfg.differentiable) return fail(GMPS_ERR_STATE, "handle was not created differentiable");
   if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
@@ -731,6 +788,7 @@ gmps_status grover_mps_backward(gmps_handle h, double dL_dP, double* grad_phi, d
 static_assert(sizeof(gmps_gate) == sizeof(GateOp), "gmps_gate and GateOp must share their layout");
 
 gmps_status grover_mps_apply_circuit(gmps_handle h, const gmps_gate* gates, int64_t count, int64_t repeat) {
+  CallRange range_("grover_mps_apply_circuit");
   if (!h) return fail(GMPS_ERR_ARG, "handle is NULL");
   if (h->error) return fail(GMPS_ERR_STATE, "handle is in an error state");
   if (count < 0 || repeat < 0) return fail(GMPS_ERR_ARG, "count and repeat must be >= 0");
@@ -753,7 +811,7 @@ gmps_status grover_mps_apply_circuit(gmps_handle h, const gmps_gate* gates, int6
     if (h->d_gates) cudaFree(h->d_gates);
     h->d_gates = nullptr;
     h->gate_cap = 0;
-    if (cudaMalloc(&h->d_gates, sizeof(GateOp) * count) != cudaSuccess) return fail(GMPS_ERR_OOM, "gate list");
+    if (dev_malloc((void**)&h->d_gates, sizeof(GateOp) * count) != cudaSuccess) return fail(GMPS_ERR_OOM, "gate list");
     h->gate_cap = count;
   }
   InstDesc d = base_desc(h, h->main);
@@ -869,6 +927,7 @@ extern "C" {
 gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const int64_t* ks,
                                     const double* const* host_phi, const double* const* host_psi,
                                     void* cuda_stream, gmps_batch_handle* out) {
+  CallRange range_("grover_mps_batch_create");
   if (!out || !cfgs || !ks || count < 1) return fail(GMPS_ERR_ARG, "bad batch arguments");
   *out = nullptr;
   gmps_batch_ctx* b = new gmps_batch_ctx();
@@ -891,21 +950,21 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
   std::vector<double> cost(count);
   for (int i = 0; i < count; ++i) {
     if ((s = validate(&cfgs[i]))) {
-      delete b;
+      grover_mps_batch_destroy(b);  // also the stream it created
       return s;
     }
     if (cfgs[i].dtype != b->dtype) {
-      delete b;
+      grover_mps_batch_destroy(b);  // also the stream it created
       return fail(GMPS_ERR_ARG, "all batch instances must share dtype");
     }
     if (ks[i] < 0) {
-      delete b;
+      grover_mps_batch_destroy(b);  // also the stream it created
       return fail(GMPS_ERR_ARG, "k must be >= 0");
     }
     b->marked[i].assign(cfgs[i].marked, cfgs[i].marked + cfgs[i].M);
     b->cfgs[i].marked = b->marked[i].data();
     if ((s = make_plan_for(&b->cfgs[i], false, &b->plans[i]))) {
-      delete b;
+      grover_mps_batch_destroy(b);  // also the stream it created
       return s;
     }
     const Plan& P = b->plans[i];
@@ -918,9 +977,9 @@ gmps_status grover_mps_batch_create(int count, const gmps_config* cfgs, const in
   }
   total += a256(sizeof(InstDesc) * count) + a256(sizeof(int)) + a256(sizeof(double) * count) +
            a256(sizeof(unsigned long long) * 64) + a256(sizeof(double) * 128);
-  cudaError_t e = cudaMalloc(&b->mem, total);
+  cudaError_t e = dev_malloc((void**)&b->mem, total);
   if (e != cudaSuccess) {
-    delete b;
+    grover_mps_batch_destroy(b);  // also the stream it created
     return fail(GMPS_ERR_OOM, "batch arena");
   }
   b->order.resize(count);
@@ -1020,6 +1079,7 @@ gmps_status grover_mps_batch_set_threads(gmps_batch_handle b, int threads) {
 }
 
 gmps_status grover_mps_batch_run(gmps_batch_handle b, int use_graph) {
+  CallRange range_("grover_mps_batch_run");
   if (!b) return fail(GMPS_ERR_ARG, "NULL handle");
   // blocks resident per SM for this CTA size and shared-memory footprint
   int dev = 0, nsm = 0, smem_sm = 0;
@@ -1152,6 +1212,7 @@ extern "C" {
 
 gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int K, void* cuda_stream,
                                          gmps_diff_batch_handle* out) {
+  CallRange range_("grover_mps_diff_batch_create");
   if (!out) return fail(GMPS_ERR_ARG, "out is NULL");
   *out = nullptr;
   gmps_status s = validate(cfg);
@@ -1187,7 +1248,7 @@ gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int 
                        a256(sizeof(double) * 2 * (size_t)count * b->every * (M + 1)) +
                        a256(sizeof(double) * count) + a256(sizeof(int)) + site_b * nslab +
                        a256(b->plan.work_bytes) * 3 * count + a256(b->plan.jc_bytes) * count;
-  cudaError_t e = cudaMalloc(&b->mem, bytes);
+  cudaError_t e = dev_malloc((void**)&b->mem, bytes);
   if (e != cudaSuccess) {
     grover_mps_diff_batch_destroy(b);
     return fail(GMPS_ERR_OOM, std::string("differentiable batch: ") + cudaGetErrorString(e));
@@ -1291,6 +1352,7 @@ gmps_status grover_mps_diff_batch_create(const gmps_config* cfg, int count, int 
 
 gmps_status grover_mps_diff_batch_run(gmps_diff_batch_handle b, const double* host_phi, const double* host_psi,
                                       double* host_loss, double* host_gphi, double* host_gpsi) {
+  CallRange range_("grover_mps_diff_batch_run");
   if (!b || !host_phi || !host_psi || !host_loss || !host_gphi || !host_gpsi)
     return fail(GMPS_ERR_ARG, "NULL argument");
   const size_t ck = (size_t)b->count * b->K;
@@ -1403,6 +1465,7 @@ extern "C" gmps_status grover_mps_run_noalloc(int n, const uint64_t* marked, int
                                               double tol, int64_t k, const double* dev_phi,
                                               const double* dev_psi, void* cuda_stream, double* p_marked,
                                               double* amp_marked, int* chi_out) {
+  CallRange range_("grover_mps_run_noalloc");
   gmps_config c{};
   c.n = n;
   c.M = M;

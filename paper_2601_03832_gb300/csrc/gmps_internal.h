@@ -166,6 +166,10 @@ GMPS_HD long long slot_elems(int l, int n, int rcap) {
   return left * 2 * right;
 }
 
+// Device allocation of the C API: cudaMalloc, or cudaErrorMemoryAllocation
+// while grover_mps_debug_fail_allocations has failures left to force.
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 // Launchers (gmps_kernels.cu).  dtype: gmps_dtype.  All enqueue on `stream`.
 cudaError_t launch_init(const InstDesc* d_desc, int count, int dtype, int threads,
                         cudaStream_t stream);

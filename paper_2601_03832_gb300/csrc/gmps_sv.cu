@@ -382,7 +382,7 @@ gmps_status grover_sv_create(int n, const uint64_t* marked, int M, int dtype, vo
   h->s.N = h->N;
   h->s.M = M;
   const size_t vb = a256(elem_bytes(dtype) * (size_t)h->N);
-  cudaError_t e = cudaMalloc(&h->amps, vb);
+  cudaError_t e = gmps::dev_malloc((void**)&h->amps, vb);
   if (e != cudaSuccess) {
     grover_sv_destroy(h);
     return fail(GMPS_ERR_OOM, std::string("statevector allocation: ") + cudaGetErrorString(e));
@@ -391,7 +391,7 @@ gmps_status grover_sv_create(int n, const uint64_t* marked, int M, int dtype, vo
                      a256(sizeof(double2) * 2) + a256(sizeof(double2) * h->s.grid) + a256(sizeof(unsigned)) +
                      a256(sizeof(long long)) + a256(sizeof(double*) * 2) + a256(sizeof(long long)) +
                      a256(sizeof(double2) * (M + 1)) + a256(sizeof(unsigned long long) * (M + 1));
-  e = cudaMalloc(&h->aux, aux);
+  e = gmps::dev_malloc((void**)&h->aux, aux);
   if (e != cudaSuccess) {
     grover_sv_destroy(h);
     return fail(GMPS_ERR_OOM, "statevector scratch");
@@ -453,7 +453,8 @@ gmps_status grover_sv_iterate(gsv_handle h, int64_t k, const double* host_phi, c
       if (h->d_ph) cudaFree(h->d_ph);
       h->d_ph = nullptr;
       h->ph_cap = 0;
-      if (cudaMalloc(&h->d_ph, sizeof(double) * 2 * k) != cudaSuccess) return fail(GMPS_ERR_OOM, "phase buffer");
+      if (gmps::dev_malloc((void**)&h->d_ph, sizeof(double) * 2 * k) != cudaSuccess)
+        return fail(GMPS_ERR_OOM, "phase buffer");
       h->ph_cap = k;
     }
     if (host_phi) {

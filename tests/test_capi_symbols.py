@@ -120,3 +120,17 @@ def test_statevector_validation_needs_no_gpu():
             B.GroverSV(**kw)
         assert e.value.status == 1
         assert text in str(e.value), (str(e.value), text)
+
+
+def test_fault_injection_hook_needs_no_gpu():
+    """grover_mps_debug_fail_allocations takes a count >= 0 and refuses a
+    negative one, without any CUDA call; 0 clears it."""
+    import pytest
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2601_03832_gb300 import binding as B
+    with pytest.raises(B.GMPSError) as e:
+        B.debug_fail_allocations(-1)
+    assert e.value.status == 1 and "count" in str(e.value)
+    B.debug_fail_allocations(3)
+    B.debug_fail_allocations(0)

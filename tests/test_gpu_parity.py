@@ -278,3 +278,43 @@ def test_autotune_picks_a_candidate_and_caches_per_device(B, tmp_path, monkeypat
     assert key.startswith(f"{props.name}|sm{props.multi_processor_count}|")
     best2, rec2 = autotune.tune_batch(insts, dtype="c64", apply="fused", kslice=4)
     assert best2 == best and rec2 == rec
+
+
+def test_forced_allocation_failure_reports_oom(B):
+    """A device allocation that fails (forced by the library's fault hook)
+    surfaces as GMPS_ERR_OOM from the handle, the batch and the statevector,
+    with nothing left behind: the next creation succeeds and runs."""
+    inst = inputs.config_small()
+    for make in (lambda: B.GroverMPS(inst.n, inst.marked, chi_max=4),
+                 lambda: B.GroverBatch([inst], dtype="c128", apply="fused"),
+                 lambda: B.GroverSV(inst.n, inst.marked)):
+        B.debug_fail_allocations(1)
+        with pytest.raises(B.GMPSError) as e:
+            make()
+        assert e.value.status == 2
+    B.debug_fail_allocations(0)
+    g = B.GroverMPS(inst.n, inst.marked, chi_max=4)
+    g.iterate(inst.k)
+    assert abs(g.prob_marked() - reduced.closed_form(inst.n, 1, inst.k)[0]) < TOL_P_F64
+    g.close()
+
+
+def test_arena_canary_catches_a_write_past_the_arena(B):
+    """The canary closing a handle's arena is checked after every call that
+    synchronises: overwriting it (here from the host, through the caller's
+    torch arena) turns the next call into GMPS_ERR_STATE."""
+    import torch
+    inst = inputs.config_small()
+    nbytes = B.arena_bytes(inst.n, inst.marked, chi_max=4)
+    buf = torch.zeros(nbytes + 256, dtype=torch.uint8, device="cuda")
+    off = (256 - buf.data_ptr() % 256) % 256
+    base = buf.data_ptr() + off
+    s = torch.cuda.current_stream()
+    g = B.GroverMPS(inst.n, inst.marked, chi_max=4, stream=s.cuda_stream, arena=(base, nbytes))
+    g.iterate(5)                                   # canary intact: fine
+    buf[off + nbytes - 8: off + nbytes] = 0xFF     # the arena's last bytes
+    torch.cuda.synchronize()
+    with pytest.raises(B.GMPSError) as e:
+        g.iterate(5)
+    assert e.value.status == 7 and "canary" in str(e.value)
+    g.close()
