@@ -35,6 +35,9 @@
  *    grover_mps_last_error().  A handle whose device work reported an error
  *    (non-convergence, non-finite norm, capacity overflow) enters an error
  *    state: every later call except stats/destroy returns GMPS_ERR_STATE.
+ *    The arena ends in a canary that every synchronising call compares; a
+ *    write past the instance's memory makes that call return GMPS_ERR_STATE
+ *    and puts the handle in the error state.
  *  - Calls on one handle are not thread-safe; different handles are
  *    independent.
  */
@@ -137,7 +140,10 @@ typedef struct gmps_stats {
 /* ------------------------------------------------------------------ */
 
 /* Device bytes the handle needs for `cfg` (arena sizing for callers that
- * allocate it themselves, e.g. from a PyTorch tensor). */
+ * allocate it themselves, e.g. from a PyTorch tensor; 256-byte aligned).
+ * Includes the closing canary (256 bytes) and, for the precision forms, the
+ * per-site cache of Jacobi rotations (about n * rcap^2 * 16 bytes per sweep
+ * pair of an iteration). */
 gmps_status grover_mps_arena_bytes(const gmps_config* cfg, size_t* bytes);
 
 /* Create a handle holding |s> = |+>^{(x)n} (Sec. II, Eq. 2) as a bond-1
