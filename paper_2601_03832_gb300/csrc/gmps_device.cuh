@@ -995,6 +995,158 @@ __device__ int jacobi_rows(cx<T>* Mat, int r, int c, int ldm, cx<T>* U, int ldu,
   return -1;
 }
 
+// LQ factorisation with row pivoting, in place, of A (r x c, r <= c, leading
+// dim ld): P A H_0 H_1 ... H_{r-1} = [L 0] with L lower triangular and
+// H_k = I - tau_k v_k v_k^dag acting on columns k..c-1 from the right (the
+// Householder reflector of the conjugated row, so that row k becomes
+// beta_k e_k).  Row k keeps u_k = conj(v_k) from column k on, beta (L's
+// diagonal) and tau are returned, L's strict lower part stays in place.
+// Pivot: the remaining row of largest norm over the trailing columns
+// (exact FP32 images, lowest row on ties); rperm[k] = the original row now at
+// position k.  rn: scratch for r norms; ctl: 1 int.
+template <class T>
+__device__ void lq_rows_pivoted(cx<T>* A, int r, int c, int ld, T* tau, cx<T>* beta, int* rperm, T* rn,
+                                int* ctl) {
+  {
+    const Grp g = make_grp(pick_g(c, r));
+    for (int t0 = 0; t0 < r; t0 += g.ng) {
+      const int i = t0 + g.gid;
+      T s2 = 0;
+      if (i < r)
+        for (int j = g.lg; j < c; j += g.G) s2 += abs2(A[i * ld + j]);
+      s2 = gsum(s2, g.G);
+      if (i < r && g.lg == 0) {
+        rn[i] = s2;
+        rperm[i] = i;
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {
+    if (threadIdx.x == 0) {
+      int best = k;
+      float bv = f32_scaled(rn[k], 0);
+      for (int i = k + 1; i < r; ++i) {
+        const float v = f32_scaled(rn[i], 0);
+        if (v > bv) {
+          bv = v;
+          best = i;
+        }
+      }
+      ctl[0] = best;
+      if (best != k) {
+        const T tn = rn[k];
+        rn[k] = rn[best];
+        rn[best] = tn;
+        const int tp = rperm[k];
+        rperm[k] = rperm[best];
+        rperm[best] = tp;
+      }
+    }
+    __syncthreads();
+    const int best = ctl[0];
+    if (best != k)
+      for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        const cx<T> t = A[k * ld + j];
+        A[k * ld + j] = A[best * ld + j];
+        A[best * ld + j] = t;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // y = conj(row k) from column k: H y = b e_0 with b = -e^{i arg y_0} |y|;
+      // the row becomes conj(b) e_0 and u = conj(y - b e_0) is the row with
+      // its first entry less conj(b)
+      const T s2 = rn[k];
+      const cx<T> x0 = A[k * ld + k];
+      const T a2 = abs2(x0);
+      cx<T> b = mk<T>(0, 0);
+      T t = 0;
+      if (s2 > K<T>::tiny2()) {
+        const T inv = rsqrt(s2);
+        const T nrm = s2 * inv;
+        cx<T> ph = mk<T>(1, 0);
+        T ax0 = 0;
+        if (a2 > K<T>::phase_floor() * s2) {
+          const T ia = rsqrt(a2);
+          ax0 = a2 * ia;
+          ph = mk<T>(x0.re * ia, -x0.im * ia);  // e^{i arg y_0}, y_0 = conj(x0)
+        }
+        b = cscale(ph, -nrm);
+        t = (T)1 / (nrm * (nrm + ax0));
+        A[k * ld + k] = csub(x0, mk<T>(b.re, -b.im));
+      }
+      beta[k] = mk<T>(b.re, -b.im);
+      tau[k] = t;
+    }
+    __syncthreads();
+    const T tk = tau[k];
+    const int ntask = r - k - 1;
+    const Grp g = make_grp(pick_g(c - k, ntask));
+    for (int t0 = 0; t0 < ntask; t0 += g.ng) {
+      const int i = k + 1 + t0 + g.gid;
+      const bool act = (t0 + g.gid) < ntask;
+      cx<T> w = mk<T>(0, 0);
+      if (act)
+        for (int j = k + g.lg; j < c; j += g.G) w = cmacc(w, A[k * ld + j], A[i * ld + j]);
+      w.re = gsum(w.re, g.G);
+      w.im = gsum(w.im, g.G);
+      T s2 = 0;
+      if (act) {
+        const cx<T> tw = cscale(w, -tk);
+        for (int j = k + g.lg; j < c; j += g.G) {
+          cx<T> x = A[i * ld + j];
+          if (tk != (T)0) x = cmac(x, tw, A[k * ld + j]);
+          A[i * ld + j] = x;
+          if (j > k) s2 += abs2(x);
+        }
+      }
+      s2 = gsum(s2, g.G);
+      if (act && g.lg == 0) rn[i] = s2;
+    }
+    __syncthreads();
+  }
+}
+
+// Q (r x c) of lq_rows_pivoted in place over its reflector rows: row k of Q
+// is e_k^T H_k H_{k-1} ... H_0, formed from the last row up (row k's
+// reflector is consumed when rows k+1.. have taken H_k); columns left of k
+// of row k are zero.  L must have been copied out first.
+template <class T>
+__device__ void lq_form_q(cx<T>* A, int r, int c, int ld, const T* tau) {
+  for (int k = r - 1; k >= 0; --k) {
+    const T tk = tau[k];
+    const int ntask = r - k - 1;
+    const Grp g = make_grp(pick_g(c - k, ntask));
+    for (int t0 = 0; t0 < ntask; t0 += g.ng) {
+      const int i = k + 1 + t0 + g.gid;
+      const bool act = (t0 + g.gid) < ntask;
+      cx<T> w = mk<T>(0, 0);
+      if (act)
+        for (int j = k + g.lg; j < c; j += g.G) w = cmacc(w, A[k * ld + j], A[i * ld + j]);
+      w.re = gsum(w.re, g.G);
+      w.im = gsum(w.im, g.G);
+      if (act && tk != (T)0) {
+        const cx<T> tw = cscale(w, -tk);
+        for (int j = k + g.lg; j < c; j += g.G) A[i * ld + j] = cmac(A[i * ld + j], tw, A[k * ld + j]);
+      }
+    }
+    __syncthreads();
+    // row k: e_k^T - tau conj(u_0) u on columns >= k
+    const cx<T> u0 = A[k * ld + k];
+    const cx<T> f = cscale(mk<T>(u0.re, -u0.im), -tk);
+    __syncthreads();
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+      cx<T> q = mk<T>(0, 0);
+      if (j >= k) {
+        q = cmul(f, A[k * ld + j]);
+        if (j == k) q.re += (T)1;
+      }
+      A[k * ld + j] = q;
+    }
+    __syncthreads();
+  }
+}
+
 // Mat (r x c, leading dim c) <- U (r x r, leading dim r) Mat in place: the
 // block holds a chunk of columns' results in registers (at most 4 per
 // thread; each output column depends on its own input column only) before
@@ -1454,26 +1606,54 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     if (fits)
       for (int e = threadIdx.x; e < rl; e += blockDim.x) fits &= (pv_cur[e] >= 0 && pv_cur[e] == pv_old[e]);
     const bool warm = __syncthreads_and(fits);
-    if (warm) {
-      for (int e = threadIdx.x; e < rl * rl; e += blockDim.x) B.U[e] = jc[e];
+    // without a cached start (FP64): precondition with a row-pivoted LQ,
+    // P Mat = [L 0] Q, i.e. the column-pivoted QR of Mat^dag with R = L^dag,
+    // and rotate the rows of X = L^dag (rl x rl, held in the U*S buffer, free
+    // until this step writes its own U*S): half the columns per rotation,
+    // and R's rows are graded by the pivoting (QR-preconditioned one-sided
+    // Jacobi, Drmac-Veselic).  With J X = S W^dag: Mat = P^T W S (J Q), so
+    // the new site is J Q and U*S = P^T (J X)^dag.  Measured: it pays from
+    // about 24 rows (n = 40, M = 32: +8.5%; 17 rows: the LQ and Q's formation
+    // cost more than the narrower rotations save)
+    bool lq = false;
+    if constexpr (std::is_same<T, double>::value)
+      lq = jc == nullptr && rl >= 24 && c >= rl && rl * rl <= d.rcap * d.chicap;
+    cx<T>* const Lb = B.US;
+    int sw;
+    if (lq) {
+      lq_rows_pivoted<T>(B.Mat, rl, c, c, B.tau, B.beta, B.qperm, B.qcn, B.misc + 8);
+      for (int e = threadIdx.x; e < rl * rl; e += blockDim.x) {  // X = L^dag
+        const int i = e / rl, j = e % rl;
+        const cx<T> x = i < j ? B.Mat[j * c + i] : (j == i ? B.beta[i] : mk<T>(0, 0));
+        Lb[e] = mk<T>(x.re, -x.im);
+      }
       __syncthreads();
-      rotate_rows<T>(B.Mat, rl, c, B.U);
-    }
-    const int sw = jacobi_rows<T>(B.Mat, rl, c, c, B.U, rl, d.max_sweeps, K<T>::jtolf(), B.tmisc[8], warm);
-    if (jc != nullptr) {
-      for (int e = threadIdx.x; e < rl * rl; e += blockDim.x) jc[e] = B.U[e];
-      for (int e = threadIdx.x; e < rl; e += blockDim.x) pv_old[e] = pv_cur[e];
-      if (threadIdx.x == 0) d.stats->jrank[bank][l] = rl;
+      lq_form_q<T>(B.Mat, rl, c, c, B.tau);
+      sw = jacobi_rows<T>(Lb, rl, rl, rl, B.U, rl, d.max_sweeps, K<T>::jtolf(), B.tmisc[8], false);
+    } else {
+      if (warm) {
+        for (int e = threadIdx.x; e < rl * rl; e += blockDim.x) B.U[e] = jc[e];
+        __syncthreads();
+        rotate_rows<T>(B.Mat, rl, c, B.U);
+      }
+      sw = jacobi_rows<T>(B.Mat, rl, c, c, B.U, rl, d.max_sweeps, K<T>::jtolf(), B.tmisc[8], warm);
+      if (jc != nullptr) {
+        for (int e = threadIdx.x; e < rl * rl; e += blockDim.x) jc[e] = B.U[e];
+        for (int e = threadIdx.x; e < rl; e += blockDim.x) pv_old[e] = pv_cur[e];
+        if (threadIdx.x == 0) d.stats->jrank[bank][l] = rl;
+      }
     }
     // row norms -> sigma, ranks -> perm
     {
-      const int G = pow2_cap32(c);
+      const cx<T>* R = lq ? Lb : B.Mat;
+      const int rc = lq ? rl : c;
+      const int G = pow2_cap32(rc);
       const Grp g = make_grp(G);
       for (int t0 = 0; t0 < rl; t0 += g.ng) {
         const int i = t0 + g.gid;
         T s2 = 0;
         if (i < rl)
-          for (int j = g.lg; j < c; j += G) s2 += abs2(B.Mat[i * c + j]);
+          for (int j = g.lg; j < rc; j += G) s2 += abs2(R[i * rc + j]);
         s2 = gsum(s2, G);
         if (i < rl && g.lg == 0) B.sig[i] = s2;  // sigma_i^2 (rows are orthogonal)
       }
@@ -1526,11 +1706,29 @@ __device__ void sweep_pair(Blk<T, S>& B, int mode, int op, int D, const cx<T>* l
     for (int e = threadIdx.x; e < k * c; e += blockDim.x) {
       const int t = e / c, j = e % c;
       const int pr = B.perm[t];
-      st_site(dst + e, cscale(B.Mat[pr * c + j], B.qcn[t]), B.key(l, 1), e);
+      cx<T> v;
+      if (lq) {  // row pr of J Q (orthonormal rows)
+        v = mk<T>(0, 0);
+        for (int a = 0; a < rl; ++a) v = cmac(v, B.U[pr * rl + a], B.Mat[a * c + j]);
+      } else {
+        v = cscale(B.Mat[pr * c + j], B.qcn[t]);
+      }
+      st_site(dst + e, v, B.key(l, 1), e);
     }
     // U S with U = J^dag (the product of the rotations is accumulated in B.U;
-    // the previous US was consumed when Mat was formed)
-    for (int e = threadIdx.x; e < rl * k; e += blockDim.x) {
+    // the previous US was consumed when Mat was formed); after the LQ it is
+    // P^T (J X)^dag: row rperm[ip] takes conj((J X)[pr][ip]), staged in the
+    // Mat buffer (Q is consumed) because J X sits in the U*S buffer
+    __syncthreads();
+    if (lq) {
+      for (int e = threadIdx.x; e < rl * k; e += blockDim.x) {
+        const cx<T> x = Lb[B.perm[e % k] * rl + e / k];
+        B.Mat[e] = mk<T>(x.re, -x.im);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < rl * k; e += blockDim.x) B.US[B.qperm[e / k] * k + e % k] = B.Mat[e];
+    }
+    for (int e = threadIdx.x; e < rl * k && !lq; e += blockDim.x) {
       const int i = e / k, t = e % k;
       const int pr = B.perm[t];
       const cx<T> u = B.U[pr * rl + i];
