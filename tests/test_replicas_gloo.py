@@ -80,3 +80,20 @@ def test_executed_flop_model_hand_count():
     assert bench.executed_flops_per_iter(2, 1, 1, "fused") == 304
     for n, chi, M, apply in ((29, 2, 1, "fused"), (40, 33, 32, "fused"), (40, 33, 32, "mpo"), (20, 5, 4, "split")):
         assert bench.executed_flops_per_iter(n, chi, M, apply) < bench.algorithmic_flops_per_iter(n, chi, M, apply)
+
+
+def test_oracle_pool_baselines_run_on_cpu():
+    """The batched and differentiable CPU baselines of the bench run the
+    oracle in spawned processes (one BLAS thread each) and report the cores
+    they used; a tiny sample of each finishes on the CPU alone."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2601_03832_gb300 import inputs
+    insts = inputs.config_batched(count=512)
+    rec = bench.cpu_baseline_batched(insts, kslice=1, count=2)
+    assert rec["kind"] == "oracle" and rec["value"] > 0 and rec["cores"] >= 1
+    assert "first 2 of the 512 instances" in rec["sample"]
+    di, phi, psi = inputs.config_differentiable(B=64)
+    small = type(di)(n=10, marked=[3, 700], k=4, chi_max=di.chi_max, tag="small")
+    rec = bench.cpu_baseline_differentiable(small, phi[:, :4], psi[:, :4], vectors=1)
+    assert rec["value"] > 0 and rec["cores"] == 1
